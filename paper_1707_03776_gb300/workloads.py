@@ -1,0 +1,158 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+Both the CUDA path and the CPU oracle consume these arrays; this module holds
+none of the method's arithmetic (no stencil, no update, no interpolation).
+Everything is generated in FP64 and rounded once to FP32, so that both sides
+see bit-identical FP32 inputs.
+
+Axis convention: fields are (n0, n1, n2) row-major with (x, y, z) -> (d0, d1,
+d2); z (depth) is the contiguous axis d2 and the surface is z = 0.
+
+Inputs defined here (the readings of the paper's unspecified `Model(...)`):
+  * velocity: two layers, 1500 m/s above half depth and 2500 m/s below;
+    square slowness m = 1/v^2 (SI units);
+  * damping eta = m * sigma with the polynomial sponge
+    sigma(x) = sum_axes sigma_max (r/W)^2 on the W cells next to every face
+    (r in (0, W] cells into the layer), sigma_max = 3 v_max ln(1/R) / (2 W h),
+    R = 1e-3; so that dt*eta/m = dt*sigma;
+  * source: Ricker wavelet (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2);
+  * diffusion: indicator of the ring 0.25 < r < 0.35 about (0.5, 0.5).
+"""
+import math
+
+import numpy as np
+
+SEED_BASE = 1707_03776
+
+
+def rng(config_id: int = 0, salt: int = 0) -> np.random.Generator:
+    return np.random.default_rng(SEED_BASE + config_id + 1000 * salt)
+
+
+def ricker(nt: int, dt: float, f0: float = 10.0, t0: float = None) -> np.ndarray:
+    """Ricker wavelet sampled at t_n = n dt, n = 0..nt-1 (FP64)."""
+    if t0 is None:
+        t0 = 1.0 / f0
+    t = np.arange(nt, dtype=np.float64) * dt
+    a = (math.pi * f0 * (t - t0)) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def two_layer_velocity(shape, v_top=1500.0, v_bottom=2500.0, interface=None) -> np.ndarray:
+    """Velocity (FP64) with v_top for depth index < interface, v_bottom below."""
+    nz = shape[-1]
+    if interface is None:
+        interface = nz // 2
+    v = np.full(shape, v_top, dtype=np.float64)
+    v[..., interface:] = v_bottom
+    return v
+
+
+def sponge_sigma(shape, spacing, width, v_max, reflection=1e-3) -> np.ndarray:
+    """Polynomial sponge damping rate sigma (1/s, FP64) on every face."""
+    sigma = np.zeros(shape, dtype=np.float64)
+    if width <= 0:
+        return sigma
+    ndim = len(shape)
+    for a in range(ndim):
+        n = shape[a]
+        h = spacing[a]
+        i = np.arange(n, dtype=np.float64)
+        r = np.maximum(0.0, np.maximum(width - i, i - (n - 1 - width)))
+        smax = 3.0 * v_max * math.log(1.0 / reflection) / (2.0 * width * h)
+        prof = smax * (r / width) ** 2
+        sh = [1] * ndim
+        sh[a] = n
+        sigma = sigma + prof.reshape(sh)
+    return sigma
+
+
+def acoustic_config(n=512, space_order=8, nt=1000, h=10.0, sponge=40, nrec_side=101,
+                    cfl=0.4, v_top=1500.0, v_bottom=2500.0, f0=10.0, ndim=3):
+    """The 3D isotropic acoustic forward workload (and its scaled-down copies).
+
+    n^3 interior grid (n^2 in 2D), spacing h, two-layer velocity, `sponge`-cell
+    sponge, dt = cfl*h/v_max, one Ricker source at the surface centre just
+    below the top sponge, nrec_side^2 receivers on the plane half a cell below
+    it (a line of nrec_side receivers in 2D).  Returns a dict of FP32 fields
+    and FP64 coordinates.
+    """
+    shape = (n,) * ndim
+    spacing = (h,) * ndim
+    origin = (0.0,) * ndim
+    v = two_layer_velocity(shape, v_top, v_bottom)
+    v_max = max(v_top, v_bottom)
+    dt = cfl * h / v_max
+    m64 = 1.0 / v ** 2
+    m = m64.astype(np.float32)
+    sigma = sponge_sigma(shape, spacing, sponge, v_max)
+    eta = (m.astype(np.float64) * sigma).astype(np.float32)
+    depth = float(sponge)
+    centre = (n - 1) / 2.0
+    if ndim == 3:
+        src_idx = np.array([[centre, centre, depth]])
+        lo, hi = float(sponge), float(n - 1 - sponge)
+        g = np.linspace(lo, hi, nrec_side)
+        gx, gy = np.meshgrid(g, g, indexing="ij")
+        rec_idx = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, depth + 0.5)], axis=1)
+    else:
+        src_idx = np.array([[centre, depth]])
+        lo, hi = float(sponge), float(n - 1 - sponge)
+        g = np.linspace(lo, hi, nrec_side)
+        rec_idx = np.stack([g, np.full(g.size, depth + 0.5)], axis=1)
+    src_coords = src_idx * h
+    rec_coords = rec_idx * h
+    src_trace = ricker(nt, dt, f0).astype(np.float32).reshape(nt, 1)
+    return dict(shape=shape, spacing=spacing, origin=origin, space_order=space_order,
+                m=m, eta=eta, dt=dt, nt=nt, src_coords=src_coords, src_trace=src_trace,
+                rec_coords=rec_coords, v_max=v_max)
+
+
+def diffusion_ring(n=256, a=0.5, nt=500, courant=0.2):
+    """2D diffusion workload: n x n nodes at i*h, h = 1/(n-1), the outer rows
+    and columns are the zero Dirichlet nodes; u0 = 1 in 0.25 < r < 0.35 about
+    (0.5, 0.5).  Returns the full n x n initial field (FP32), the interior
+    (n-2) x (n-2) view's parameters and dt = courant*h^2/a."""
+    h = 1.0 / (n - 1)
+    x = np.arange(n, dtype=np.float64) * h
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    r2 = (X - 0.5) ** 2 + (Y - 0.5) ** 2
+    u0 = ((r2 > 0.25 ** 2) & (r2 < 0.35 ** 2)).astype(np.float32)
+    dt = courant * h * h / a
+    return dict(u0_full=u0, u0=np.ascontiguousarray(u0[1:-1, 1:-1]), shape=(n - 2, n - 2),
+                spacing=(h, h), origin=(h, h), a=a, dt=dt, nt=nt, space_order=2)
+
+
+def random_field(shape, seed, scale=1.0, smooth=0):
+    """Seeded FP32 random field; `smooth` passes of a 3-point box filter per axis."""
+    g = np.random.default_rng(SEED_BASE + 7919 * seed)
+    u = g.standard_normal(shape)
+    for _ in range(smooth):
+        for a in range(len(shape)):
+            u = (np.roll(u, 1, a) + u + np.roll(u, -1, a)) / 3.0
+    return (scale * u).astype(np.float32)
+
+
+def random_points(shape, spacing, origin, npoint, seed, margin=0.0):
+    """Seeded off-grid coordinates inside [origin, origin + (n-1) h] (FP64)."""
+    g = np.random.default_rng(SEED_BASE + 104729 * seed)
+    ndim = len(shape)
+    lo = np.array(origin, dtype=np.float64) + margin * np.array(spacing)
+    hi = np.array(origin, dtype=np.float64) + (np.array(shape) - 1 - margin) * np.array(spacing)
+    return lo + (hi - lo) * g.random((npoint, ndim))
+
+
+def random_smooth_velocity(shape, seed, sigma_cells=8.0, vmin=1500.0, vmax=4500.0):
+    """Seeded Gaussian-filtered noise rescaled to [vmin, vmax] (FP64)."""
+    g = np.random.default_rng(SEED_BASE + 31337 * seed)
+    u = g.standard_normal(shape)
+    # separable Gaussian filter by FFT along each axis
+    for a in range(len(shape)):
+        n = shape[a]
+        k = np.fft.rfftfreq(n)
+        filt = np.exp(-0.5 * (2 * math.pi * k * sigma_cells) ** 2)
+        sh = [1] * len(shape)
+        sh[a] = filt.size
+        u = np.fft.irfft(np.fft.rfft(u, axis=a) * filt.reshape(sh), n=n, axis=a)
+    u = (u - u.min()) / (u.max() - u.min())
+    return vmin + (vmax - vmin) * u
