@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: 3D isotropic acoustic forward modelling, 512^3, SO8, 1000 steps.
+
+One bench step is one whole forward run of the hot path on synthetic inputs
+shaped like the paper's 512^3 benchmark: coefficient preparation
+(c = dt^2/m, d = dt*eta/m), then 1000 time steps of receiver interpolation
+(101 x 101 receivers), the SO8 leapfrog update with sponge damping, and
+Ricker source injection.  Inputs (fields of 0.5 GB each) are resident in HBM
+and larger than L2, so no L2 flush is needed between steps.
+
+Printed (rank 0): one JSON line with the throughput in GPts/s (interior points
+x time steps / second), the roofline of the grid-update kernel (HBM bound, 20
+algorithmic bytes per point per step), the CPU oracle timed on this host's
+cores on a bounded sample, an end-to-end figure through the host-buffer API,
+kernel launches in the timed region and the SM clocks seen meanwhile.
+
+`--impl reference` times the CPU oracle instead (the only reference this
+paper has: there is no reference code), on bounded samples of the same
+workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D acoustic SO8 GPts/s & %HBM roofline; learned/batched vs plain at equal error"
+BYTES_PER_POINT = 20  # read u^n, u^{n-1}, c, d; write u^{n+1} (FP32)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=512)
+    p.add_argument("--so", type=int, default=8)
+    p.add_argument("--nt", type=int, default=1000)
+    p.add_argument("--cpu-steps", type=int, default=3, help="time steps in the CPU-oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(n, so, nt):
+    return "acoustic3d_%d^3_so%d_nt%d_1src_101x101rec_sponge40" % (n, so, nt)
+
+
+def config_dict(args):
+    return {"workload": workload_name(args.n, args.so, args.nt), "grid": [args.n] * 3, "space_order": args.so,
+            "time_order": 2, "nt": args.nt, "h_m": 10.0, "cfl": 0.4, "velocity": "1500/2500 m/s two-layer",
+            "sponge_cells": 40, "sources": 1, "receivers": 101 * 101,
+            "l2": "inputs larger than L2 (0.5 GB per field), no flush",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(cfg, so, steps, precision="f32"):
+    """Time `steps` oracle time steps of the forward run on the full grid."""
+    import numpy as np
+    import oracle
+    n_total = cfg["nt"]
+    t = time.perf_counter()
+    oracle.acoustic_forward(cfg["shape"], cfg["spacing"], cfg["origin"], so, cfg["m"], cfg["eta"], cfg["dt"],
+                            steps, src_coords=cfg["src_coords"], src_trace=cfg["src_trace"],
+                            rec_coords=cfg["rec_coords"], n_total=n_total, precision=precision)
+    dt = time.perf_counter() - t
+    pts = float(np.prod(cfg["shape"])) * steps
+    return pts / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1707_03776_gb300 import workloads as wl
+    oracle._lib()
+    cfg = wl.acoustic_config(n=args.n, space_order=args.so, nt=args.nt)
+    steps_per = max(1, args.cpu_steps)
+    for _ in range(args.warmup):
+        oracle_sample(cfg, args.so, steps_per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(cfg, args.so, steps_per)
+    el = time.perf_counter() - t0
+    value = args.n ** 3 * steps_per * args.steps / el / 1e9
+    sample = "%d of %d time steps of the forward run per bench step, full %d^3 grid, FP32 loop nest" % (
+        steps_per, args.nt, args.n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(args),
+            "cpu_baseline": {"value": value, "unit": "GPts/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GPts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "the paper ships no code; the reference arm is the plain CPU oracle (OpenMP loop nest)"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(REASONS, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(so):
+    """DRAM bytes per launch of the grid-update kernel from the committed ncu
+    summary, if it was taken on the kernel source as it is now."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1707_03776_gb300", "csrc", "k_tma.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        entry = rec.get("so%d" % so)
+        if entry and entry.get("source_sha") == sha:
+            return float(entry["bytes_per_launch_512"])
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    from paper_1707_03776_gb300.modeling import AcousticModel
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cfg = wl.acoustic_config(n=args.n, space_order=args.so, nt=args.nt)
+    flags = fd.FD_FLAG_PLAIN_KERNELS if args.plain else 0
+    model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], args.so, cfg["src_coords"],
+                          cfg["rec_coords"], args.nt, flags=flags)
+    m_h = torch.from_numpy(cfg["m"]).pin_memory()
+    eta_h = torch.from_numpy(cfg["eta"]).pin_memory()
+    src_h = torch.from_numpy(cfg["src_trace"]).pin_memory()
+    model.load(m_h, eta_h, src_h)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    op = model.op
+
+    def step():
+        # coefficients are recomputed every step (a2), then the whole time loop
+        op.bind("eta", model.eta)
+        model.run(cfg["dt"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    op.sync()
+
+    op.profile(args.steps * args.nt)
+    launches0 = op.launches
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = op.launches - launches0
+    op.sync()
+    k_ms, k_n = op.profile_read()
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    pts = float(args.n) ** 3 * args.nt
+    value = pts * args.steps * world / (ms_max * 1e-3) / 1e9
+
+    # receivers must hold a finite, non-trivial shot record
+    rec = model.rec.data[:, : model.rec.npoint]
+    assert torch.isfinite(rec).all().item() and rec.abs().max().item() > 0
+
+    e2e = None
+    if not args.no_e2e:
+        e_steps = max(1, min(args.steps, 2))
+        model.forward(m_h, eta_h, src_h, cfg["dt"])  # warm
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            out = model.forward(m_h, eta_h, src_h, cfg["dt"])
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        el_t = torch.tensor([el], device="cuda")
+        if world > 1:
+            dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": pts * e_steps * world / float(el_t.item()) / 1e9, "unit": "GPts/s",
+               "h2d_bytes_per_step": model.h2d_bytes(), "d2h_bytes_per_step": model.d2h_bytes(),
+               "steps": e_steps, "api": "AcousticModel.forward (host pinned m, eta, wavelet -> host traces)"}
+        assert out.shape[0] == args.nt
+
+    peak, peak_kind = measured_peak_hbm()
+    roof = None
+    if k_n > 0:
+        avg_s = k_ms / k_n * 1e-3
+        achieved = BYTES_PER_POINT * float(args.n) ** 3 / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": kernel_traffic(args.so), "peak_kind": peak_kind,
+                "kernel": "acoustic grid update (%s)" % ("plain" if args.plain else "tiled TMA"),
+                "kernel_ms_avg": k_ms / k_n, "kernel_launches_timed": k_n,
+                "algorithmic_bytes_per_launch": BYTES_PER_POINT * args.n ** 3,
+                "kernel_share_of_step": (k_ms / ms) if ms > 0 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle._lib()
+        v, el = oracle_sample(cfg, args.so, args.cpu_steps)
+        cpu = {"value": v, "unit": "GPts/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "%d of %d time steps of the same %d^3 SO%d forward run, FP32 loop nest, %.1f s" % (
+                   args.cpu_steps, args.nt, args.n, args.so, el)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(args), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk,
+                "device": torch.cuda.get_device_name(local)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

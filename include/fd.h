@@ -1,0 +1,270 @@
+/*
+ * fd.h -- C ABI of the GB300-native explicit finite-difference library
+ * (libfdgb.so), after "Optimised finite difference computation from symbolic
+ * equations" (arXiv 1707.03776).
+ *
+ * The paper states the problem as: symbolic data objects that own their data
+ * (TimeData, DenseData, PointData; Design and API section), an Operator built
+ * from update equations and grid spacings (`Operator(..., subs={h: dx,
+ * s: dt})`), applied for a number of time steps (`op(time=N)`, Linear
+ * Convection section), whose data can be rebound by name (Laplace equation
+ * section), and sparse points that inject into and interpolate from the grid
+ * (Seismic Inversion Example).  The calls below are that statement, in C:
+ *
+ *   fd_weights*          FD coefficients (the `dx2`/`laplace`/`dxl`/`dt`
+ *                        shorthands), FP64, host only
+ *   fd_grid_*            the discretised domain: shape, spacing, origin
+ *   fd_field_*           TimeData (2 time slots) / DenseData (1 slot) over
+ *                        caller-owned device memory
+ *   fd_sparse_*          PointData: off-grid coordinates + a device trace
+ *   fd_operator_*        the Operator: build, rebind, apply for nt steps
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an fd_status; FD_OK is 0.  On failure a thread-local
+ *     message is available from fd_last_error().  No C++ exception crosses
+ *     this boundary.
+ *   - Device memory belongs to the caller (e.g. PyTorch).  The library never
+ *     frees caller memory.  Handles belong to the caller and are released with
+ *     the matching *_destroy.  The library owns only its scratch: the
+ *     coefficient fields c = dt^2/m and d = dt*eta/m of an acoustic operator,
+ *     the interpolation tables of a sparse object and one status word per
+ *     operator, allocated with cudaMallocAsync on the stream given and freed on
+ *     destroy.
+ *   - Work is enqueued asynchronously on the caller's CUDA stream.  Errors
+ *     raised by kernels surface as FD_ERR_CUDA or FD_ERR_TIMEOUT at the next
+ *     fd_operator_sync.
+ *   - Floating-point data on the device is FP32.  Coordinates, spacings,
+ *     weights and dt cross the boundary as FP64 host values.
+ *
+ * Axis convention: a grid has ndim = 2 or 3 axes (d0, d1[, d2]); the last
+ * axis is contiguous in memory.  The seismic workloads map (x, y, z) to
+ * (d0, d1, d2), with depth z contiguous.
+ */
+#ifndef FD_H
+#define FD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef enum {
+    FD_OK = 0,
+    FD_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad name */
+    FD_ERR_UNSUPPORTED = 2,   /* valid request this library does not implement */
+    FD_ERR_LAYOUT = 3,        /* strides or alignment differ from fd_field_layout */
+    FD_ERR_OUT_OF_DOMAIN = 4, /* a sparse point lies outside the grid */
+    FD_ERR_UNSTABLE = 5,      /* dt above the stability limit of the scheme */
+    FD_ERR_CUDA = 6,          /* a CUDA runtime or driver call failed */
+    FD_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+    FD_ERR_NOMEM = 8          /* device or host allocation failed */
+} fd_status;
+
+/* Static English name of a status code. */
+const char *fd_status_string(fd_status status);
+/* Message of the last failing call on this thread ("" if none).  The pointer
+ * stays valid until the next failing call on the same thread. */
+const char *fd_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int fd_version(void);
+
+/* ------------------------------------------------------------------------
+ * FD weights (host, FP64)
+ * ------------------------------------------------------------------------ */
+
+/* Weights of the derivative of order `deriv` at x = 0 from samples at the `n`
+ * offsets (in grid units, distinct): sum_j w_j f(x_j) = f^(deriv)(0) h^deriv
+ * + O(h^n).  These are the coefficients behind the paper's derivative
+ * shorthands (`u.dxl` = offsets {-1, 0}, `u.dt` = {0, 1}, `u.dt2` =
+ * {-1, 0, 1}; Linear Convection and Seismic Inversion Example sections).
+ * Computed with Fornberg's recurrence (Math. Comp. 51, 1988).
+ * weights_out: n doubles.  Errors: FD_ERR_INVALID_ARG for n < 1, n > 64,
+ * deriv < 0 or deriv >= n, null pointers, repeated offsets. */
+fd_status fd_weights(int deriv, int n, const double *offsets, double *weights_out);
+
+/* Central second-derivative weights of even space order SO = 2M in [2, 16]:
+ * w_out[k] for k = 0..M, the stencil being sum_{k=-M..M} w_{|k|} f(x + k h)
+ * = h^2 f''(x) + O(h^{SO+2}) -- the `dx2` shorthand and, summed over axes,
+ * `u.laplace` (Laplace equation and Seismic Inversion Example sections).
+ * Errors: FD_ERR_UNSUPPORTED for odd or out-of-range orders. */
+fd_status fd_weights_central2(int space_order, double *w_out);
+
+/* ------------------------------------------------------------------------
+ * Grid
+ * ------------------------------------------------------------------------ */
+
+typedef struct fd_grid fd_grid;
+
+/* A regular grid of ndim = 2 or 3 axes with shape[a] >= 2 interior nodes,
+ * spacing[a] > 0 and node 0 at origin[a] (origin may be NULL: all zero).
+ * Node i of axis a sits at origin[a] + i * spacing[a].  The grid is
+ * surrounded by an implicit zero halo (zero Dirichlet ghost nodes) as wide as
+ * any stencil needs; nothing of the halo is stored.
+ * Errors: FD_ERR_INVALID_ARG. */
+fd_status fd_grid_create(int ndim, const int64_t *shape, const double *spacing,
+                         const double *origin, fd_grid **out);
+void fd_grid_destroy(fd_grid *grid);
+
+/* ------------------------------------------------------------------------
+ * Fields (TimeData / DenseData)
+ * ------------------------------------------------------------------------ */
+
+typedef struct fd_field fd_field;
+
+/* Memory layout a field of this grid must have, so that the caller (e.g.
+ * torch) can allocate it.  One time slot is a row-major FP32 array of
+ * padded_shape (ndim entries); the last axis is padded to a multiple of 8
+ * elements (32 bytes) so every row starts 32-byte aligned; pad elements are
+ * never read or written.  strides[a] (in elements) and interior_offset
+ * (always 0: no halo is stored) describe it.  The layout does not depend on
+ * the space order; `space_order` is checked (even, 2..16) and otherwise
+ * unused.  Base pointers must be 32-byte aligned. */
+fd_status fd_field_layout(const fd_grid *grid, int space_order, int64_t *padded_shape,
+                          int64_t *strides, int64_t *interior_offset);
+
+/* Wrap caller-owned device memory as a field of `levels` time slots: 2 for a
+ * time-dependent field (TimeData with time_order 2 or a ping-pong pair), 1 for
+ * a static one (DenseData: m, eta).  dev_ptrs: `levels` device pointers, each
+ * one slot in the layout of fd_field_layout (strides must be equal to it:
+ * FD_ERR_LAYOUT otherwise; pass NULL to assert the layout).  Contents are not
+ * touched.  The grid must outlive the field.
+ * Errors: FD_ERR_INVALID_ARG, FD_ERR_LAYOUT (strides or 32-byte alignment). */
+fd_status fd_field_wrap(const fd_grid *grid, int levels, void *const *dev_ptrs,
+                        const int64_t *strides, fd_field **out);
+void fd_field_destroy(fd_field *field);
+
+/* ------------------------------------------------------------------------
+ * Sparse points (PointData)
+ * ------------------------------------------------------------------------ */
+
+typedef struct fd_sparse fd_sparse;
+
+/* `npoint` off-grid points with host FP64 coordinates [npoint][ndim] in the
+ * grid's physical units, and a caller-owned FP32 device trace holding row n
+ * (time t_n = n dt) at dev_trace + n * trace_stride, n = 0..nt-1, columns
+ * 0..npoint-1 (trace_stride >= npoint).  This is the paper's PointData with
+ * `data` time-major (the transpose of its (npoint, ntime) view).
+ * The linear-interpolation table (bilinear in 2D, trilinear in 3D) is built
+ * here in FP64 and stored on the device rounded to FP32: per axis
+ * s = (x - origin)/h, i = floor(s) clamped to [0, n-2], f = s - i, the 2^ndim
+ * surrounding nodes weighted by products of f and 1 - f.  The table is
+ * uploaded on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * npoint may be 0.
+ * Errors: FD_ERR_INVALID_ARG, FD_ERR_OUT_OF_DOMAIN (a point outside
+ * [origin, origin + (n-1) h] on some axis), FD_ERR_NOMEM, FD_ERR_CUDA. */
+fd_status fd_sparse_create(const fd_grid *grid, int npoint, const double *coords,
+                           void *dev_trace, int64_t nt, int64_t trace_stride,
+                           void *cuda_stream, fd_sparse **out);
+/* Point the sparse object at another trace buffer of the same geometry. */
+fd_status fd_sparse_set_trace(fd_sparse *sparse, void *dev_trace, int64_t nt,
+                              int64_t trace_stride);
+void fd_sparse_destroy(fd_sparse *sparse);
+
+/* ------------------------------------------------------------------------
+ * Operator
+ * ------------------------------------------------------------------------ */
+
+typedef struct fd_operator fd_operator;
+
+enum {
+    /* u^{n+1} = u^n + a dt L u^n: explicit Euler for u_t = a lap u (the
+     * paper's `u.dt` with `u.laplace`).  u: 2 slots, ping-pong: step n reads
+     * slot n%2 and writes slot (n+1)%2.  Needs `a`; m, eta, src, rec unused. */
+    FD_DIFFUSION_EULER = 1,
+    /* m u_tt + eta u_t - lap u = q (Seismic Inversion Example, forward
+     * operator), centred second and backward first difference in time:
+     *   rec[n]  = R u^n                       (rec.interpolate(expr=u))
+     *   u^{n+1} = 2u^n - u^{n-1} + c L u^n - d (u^n - u^{n-1})
+     *   u^{n+1} += c Q^T src[n]               (src.inject(u, src*dt^2/m))
+     * with c = dt^2/m and d = dt*eta/m evaluated at each node.  u: 2 slots,
+     * slot n%2 holds u^n; step n overwrites slot (n+1)%2 (u^{n-1}) with
+     * u^{n+1}.  Needs m; eta, src, rec optional. */
+    FD_ACOUSTIC_LEAPFROG = 2
+};
+
+enum {
+    /* Run the time index backward: step n (n = t0+nt-1 down to t0) reads the
+     * state of time n+1 from slot (n+1)%2 and time n+2 from slot n%2 and
+     * writes time n into slot n%2, interpolating into rec[n] from the state
+     * of time n+1 and injecting src[n] into the new state.  With the roles
+     * of the point sets swapped (src = receiver data, rec = adjoint source)
+     * this is the exact transpose of the forward run -- the paper's adjoint
+     * operator with `time_axis=Backward`. */
+    FD_FLAG_REVERSE = 1u << 0,
+    /* Skip the stability check of fd_operator_apply. */
+    FD_FLAG_NO_CFL_CHECK = 1u << 1,
+    /* Use the plain one-thread-per-column kernels instead of the tiled TMA
+     * kernels (same results within FP32 rounding; for comparison). */
+    FD_FLAG_PLAIN_KERNELS = 1u << 2
+};
+
+typedef struct {
+    int kind;              /* FD_DIFFUSION_EULER or FD_ACOUSTIC_LEAPFROG */
+    int space_order;       /* even, 2..16 */
+    fd_field *u;           /* 2-slot time field */
+    fd_field *m;           /* 1-slot square slowness (acoustic) */
+    fd_field *eta;         /* 1-slot damping (acoustic, may be NULL) */
+    double a;              /* diffusivity (diffusion) */
+    fd_sparse *src;        /* injected points (acoustic, may be NULL) */
+    fd_sparse *rec;        /* interpolated points (acoustic, may be NULL) */
+    void *cuda_stream;     /* cudaStream_t all work is enqueued on */
+    unsigned flags;        /* FD_FLAG_* */
+} fd_op_desc;
+
+/* Build an operator.  All fields and sparse objects must belong to grids of
+ * the same shape.  For an acoustic operator this allocates the coefficient
+ * fields c and d (2 FP32 slots) and reduces min(m) on the device for the
+ * stability check (one stream synchronisation).
+ * Errors: FD_ERR_INVALID_ARG, FD_ERR_UNSUPPORTED (kind/order/ndim),
+ * FD_ERR_NOMEM, FD_ERR_CUDA. */
+fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **out);
+
+/* Rebind one input by name, as the paper's `op(u=u, ...)` keyword arguments:
+ * "u", "m", "eta" (obj is an fd_field*), "src", "rec" (fd_sparse*), "stream"
+ * (a cudaStream_t), "a" (a const double*).  Geometry must match. */
+fd_status fd_operator_bind(fd_operator *op, const char *name, void *obj);
+
+/* Run nt >= 0 time steps n = t0 .. t0+nt-1 (the paper's `op(time=nt)`), or
+ * n = t0+nt-1 down to t0 with FD_FLAG_REVERSE, with time step dt > 0.  Trace
+ * rows t0..t0+nt-1 of src/rec must exist.  Enqueues the work on the
+ * operator's stream and returns without waiting.  The coefficient fields are
+ * recomputed when dt or m/eta changed since the last apply.
+ * Errors (checked on the host before any launch): FD_ERR_INVALID_ARG,
+ * FD_ERR_UNSTABLE (acoustic: dt above 2 / sqrt(max_theta lambda(theta) /
+ * min m), the undamped leapfrog limit; diffusion: a dt above the explicit
+ * Euler limit 2 / (a max lambda)), FD_ERR_CUDA. */
+fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt);
+
+/* Wait for the operator's stream and report any deferred device error:
+ * FD_ERR_CUDA for a failed launch or kernel, FD_ERR_TIMEOUT when a kernel's
+ * bounded wait gave up (the status word is then cleared). */
+fd_status fd_operator_sync(fd_operator *op);
+void fd_operator_destroy(fd_operator *op);
+
+/* Number of kernel launches the library has enqueued on this operator since
+ * it was created (for launch accounting). */
+int64_t fd_operator_launch_count(const fd_operator *op);
+
+/* Stencil-kernel timing.  fd_operator_profile(op, n) brackets each of the
+ * next n launches of the operator's grid-update kernel (the kernel that does
+ * the FD update of every grid point) with CUDA events on the operator's
+ * stream; n = 0 stops and discards.  fd_operator_profile_read waits for the
+ * stream and returns the summed device time (ms) of the bracketed launches
+ * and their number.  Errors: FD_ERR_INVALID_ARG, FD_ERR_NOMEM, FD_ERR_CUDA. */
+fd_status fd_operator_profile(fd_operator *op, int64_t max_launches);
+fd_status fd_operator_profile_read(fd_operator *op, double *total_ms, int64_t *launches);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_H */

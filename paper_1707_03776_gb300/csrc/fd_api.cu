@@ -1,0 +1,690 @@
+// C-ABI of libfdgb: grids, fields, sparse points and operators (include/fd.h).
+//
+// Host logic only: validation, layouts, interpolation tables, the stability
+// check and the per-step launch sequence.  All arithmetic on grid data runs
+// in the kernel files.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fd_internal.h"
+#include "fd_internal_host.h"
+#include "fd_tma.h"
+
+struct fd_grid {
+    int ndim;
+    int64_t shape[3];
+    double spacing[3];
+    double origin[3];
+};
+
+struct fd_field {
+    fd_grid g;
+    int levels;
+    float *slot[2];
+};
+
+struct fd_sparse {
+    fd_grid g;
+    int npoint;
+    int64_t *d_base;   // library-owned
+    float *d_weight;   // library-owned, [npoint][8]
+    float *trace;      // caller-owned, row n at trace + n * stride
+    int64_t nt;
+    int64_t stride;
+    cudaStream_t alloc_stream;
+    fdgb::SparseDev dev;
+};
+
+struct fd_operator {
+    int kind;
+    int so;
+    fd_field *u, *m, *eta;
+    double a;
+    fd_sparse *src, *rec;
+    cudaStream_t stream;
+    unsigned flags;
+    fdgb::Geom geom;
+    fdgb::Coef coef;
+    double lambda_max;     // max over theta of the Laplacian symbol (1/length^2)
+    float *c, *d;          // acoustic coefficient fields (library-owned)
+    int *status;           // device status word (library-owned)
+    double coef_dt;        // dt the coefficient fields were computed for (<0: none)
+    double m_min;          // min(m) over the grid
+    int64_t launches;
+    fdgb::TmaPlan tma;     // tiled-kernel plan (tensor maps, tiling)
+    // stencil-kernel timing (fd_operator_profile)
+    std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
+    int64_t prof_max;
+    int64_t prof_used;
+};
+
+namespace fdgb {
+
+static thread_local std::string g_last_error;
+
+fd_status set_error(fd_status status, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+static fd_status cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(FD_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define FD_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return fdgb::cuda_error(e_, what); \
+    } while (0)
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Row pitch (elements) of the contiguous axis.
+static int64_t row_pitch(const fd_grid &g) { return round_up(g.shape[g.ndim - 1], 8); }
+
+static void layout_of(const fd_grid &g, int64_t *padded, int64_t *strides)
+{
+    int64_t S = row_pitch(g);
+    if (g.ndim == 3) {
+        padded[0] = g.shape[0]; padded[1] = g.shape[1]; padded[2] = S;
+        strides[0] = g.shape[1] * S; strides[1] = S; strides[2] = 1;
+    } else {
+        padded[0] = g.shape[0]; padded[1] = S;
+        strides[0] = S; strides[1] = 1;
+    }
+}
+
+static int64_t slot_elems(const fd_grid &g)
+{
+    int64_t S = row_pitch(g);
+    return g.ndim == 3 ? g.shape[0] * g.shape[1] * S : g.shape[0] * S;
+}
+
+static Geom geom_of(const fd_grid &g)
+{
+    Geom q;
+    q.ndim = g.ndim;
+    int64_t S = row_pitch(g);
+    if (g.ndim == 3) {
+        q.n[0] = g.shape[0]; q.n[1] = g.shape[1]; q.n[2] = g.shape[2];
+        q.s0 = g.shape[1] * S; q.s1 = S;
+    } else {
+        q.n[0] = 1; q.n[1] = g.shape[0]; q.n[2] = g.shape[1];
+        q.s0 = g.shape[0] * S; q.s1 = S;
+    }
+    return q;
+}
+
+static bool same_shape(const fd_grid &a, const fd_grid &b)
+{
+    if (a.ndim != b.ndim) return false;
+    for (int i = 0; i < a.ndim; i++)
+        if (a.shape[i] != b.shape[i]) return false;
+    return true;
+}
+
+// Max over theta in [0, pi] of -(w0 + 2 sum_k w_k cos(k theta)): the largest
+// eigenvalue magnitude of the 1D central stencil (in units of 1/h^2).
+static double symbol_max(const double *w, int M)
+{
+    double best = 0.0;
+    const int samples = 4096;
+    for (int s = 0; s <= samples; s++) {
+        double th = M_PI * s / samples;
+        double v = w[0];
+        for (int k = 1; k <= M; k++) v += 2.0 * w[k] * std::cos(k * th);
+        if (-v > best) best = -v;
+    }
+    return best;
+}
+
+}  // namespace fdgb
+
+using namespace fdgb;
+
+// ---------------------------------------------------------------------------
+// status and version
+// ---------------------------------------------------------------------------
+
+extern "C" const char *fd_status_string(fd_status s)
+{
+    switch (s) {
+    case FD_OK: return "FD_OK";
+    case FD_ERR_INVALID_ARG: return "FD_ERR_INVALID_ARG";
+    case FD_ERR_UNSUPPORTED: return "FD_ERR_UNSUPPORTED";
+    case FD_ERR_LAYOUT: return "FD_ERR_LAYOUT";
+    case FD_ERR_OUT_OF_DOMAIN: return "FD_ERR_OUT_OF_DOMAIN";
+    case FD_ERR_UNSTABLE: return "FD_ERR_UNSTABLE";
+    case FD_ERR_CUDA: return "FD_ERR_CUDA";
+    case FD_ERR_TIMEOUT: return "FD_ERR_TIMEOUT";
+    case FD_ERR_NOMEM: return "FD_ERR_NOMEM";
+    }
+    return "FD_ERR_UNKNOWN";
+}
+
+extern "C" const char *fd_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int fd_version(void) { return 100; }
+
+// ---------------------------------------------------------------------------
+// grid
+// ---------------------------------------------------------------------------
+
+extern "C" fd_status fd_grid_create(int ndim, const int64_t *shape, const double *spacing,
+                                    const double *origin, fd_grid **out)
+{
+    if (!out || !shape || !spacing) return set_error(FD_ERR_INVALID_ARG, "fd_grid_create: null pointer");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return set_error(FD_ERR_INVALID_ARG, "fd_grid_create: ndim must be 2 or 3");
+    fd_grid g;
+    std::memset(&g, 0, sizeof g);
+    g.ndim = ndim;
+    for (int a = 0; a < ndim; a++) {
+        if (shape[a] < 2 || shape[a] > (int64_t(1) << 24))
+            return set_error(FD_ERR_INVALID_ARG, "fd_grid_create: shape[%d] = %lld out of [2, 2^24]", a,
+                             (long long)shape[a]);
+        if (!(spacing[a] > 0.0) || !std::isfinite(spacing[a]))
+            return set_error(FD_ERR_INVALID_ARG, "fd_grid_create: spacing[%d] must be > 0", a);
+        g.shape[a] = shape[a];
+        g.spacing[a] = spacing[a];
+        g.origin[a] = origin ? origin[a] : 0.0;
+        if (!std::isfinite(g.origin[a])) return set_error(FD_ERR_INVALID_ARG, "fd_grid_create: bad origin");
+    }
+    int64_t total = 1;
+    for (int a = 0; a < ndim; a++) total *= shape[a];
+    if (total > (int64_t(1) << 40)) return set_error(FD_ERR_INVALID_ARG, "fd_grid_create: grid too large");
+    fd_grid *p = new (std::nothrow) fd_grid(g);
+    if (!p) return set_error(FD_ERR_NOMEM, "fd_grid_create: out of host memory");
+    *out = p;
+    return FD_OK;
+}
+
+extern "C" void fd_grid_destroy(fd_grid *g) { delete g; }
+
+// ---------------------------------------------------------------------------
+// fields
+// ---------------------------------------------------------------------------
+
+extern "C" fd_status fd_field_layout(const fd_grid *g, int space_order, int64_t *padded_shape,
+                                     int64_t *strides, int64_t *interior_offset)
+{
+    if (!g || !padded_shape || !strides) return set_error(FD_ERR_INVALID_ARG, "fd_field_layout: null pointer");
+    if (space_order < 2 || space_order > 16 || space_order % 2)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_field_layout: space order must be even, 2..16");
+    layout_of(*g, padded_shape, strides);
+    if (interior_offset) *interior_offset = 0;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_field_wrap(const fd_grid *g, int levels, void *const *dev_ptrs,
+                                   const int64_t *strides, fd_field **out)
+{
+    if (!g || !dev_ptrs || !out) return set_error(FD_ERR_INVALID_ARG, "fd_field_wrap: null pointer");
+    *out = nullptr;
+    if (levels != 1 && levels != 2) return set_error(FD_ERR_INVALID_ARG, "fd_field_wrap: levels must be 1 or 2");
+    int64_t padded[3], st[3];
+    layout_of(*g, padded, st);
+    if (strides)
+        for (int a = 0; a < g->ndim; a++)
+            if (strides[a] != st[a])
+                return set_error(FD_ERR_LAYOUT, "fd_field_wrap: stride[%d] = %lld, layout needs %lld", a,
+                                 (long long)strides[a], (long long)st[a]);
+    fd_field f;
+    f.g = *g;
+    f.levels = levels;
+    f.slot[0] = f.slot[1] = nullptr;
+    for (int l = 0; l < levels; l++) {
+        if (!dev_ptrs[l]) return set_error(FD_ERR_INVALID_ARG, "fd_field_wrap: null slot %d", l);
+        if (((uintptr_t)dev_ptrs[l]) % 32 != 0)
+            return set_error(FD_ERR_LAYOUT, "fd_field_wrap: slot %d is not 32-byte aligned", l);
+        f.slot[l] = (float *)dev_ptrs[l];
+    }
+    if (levels == 2 && f.slot[0] == f.slot[1])
+        return set_error(FD_ERR_INVALID_ARG, "fd_field_wrap: the two slots alias");
+    fd_field *p = new (std::nothrow) fd_field(f);
+    if (!p) return set_error(FD_ERR_NOMEM, "fd_field_wrap: out of host memory");
+    *out = p;
+    return FD_OK;
+}
+
+extern "C" void fd_field_destroy(fd_field *f) { delete f; }
+
+// ---------------------------------------------------------------------------
+// sparse points
+// ---------------------------------------------------------------------------
+
+extern "C" fd_status fd_sparse_create(const fd_grid *g, int npoint, const double *coords,
+                                      void *dev_trace, int64_t nt, int64_t trace_stride,
+                                      void *cuda_stream, fd_sparse **out)
+{
+    if (!g || !out) return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: null pointer");
+    *out = nullptr;
+    if (npoint < 0) return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: npoint < 0");
+    if (npoint > 0 && (!coords || !dev_trace))
+        return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: null coordinates or trace");
+    if (nt < 0 || (npoint > 0 && trace_stride < npoint))
+        return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: need nt >= 0 and trace_stride >= npoint");
+    const int ndim = g->ndim;
+    int64_t padded[3], st[3];
+    layout_of(*g, padded, st);
+    std::vector<int64_t> base((size_t)npoint);
+    std::vector<float> weight((size_t)npoint * 8, 0.0f);
+    for (int p = 0; p < npoint; p++) {
+        int64_t lin = 0;
+        double frac[3] = {0, 0, 0};
+        for (int a = 0; a < ndim; a++) {
+            double x = coords[(int64_t)p * ndim + a];
+            double s = (x - g->origin[a]) / g->spacing[a];
+            double top = (double)(g->shape[a] - 1);
+            if (!(s >= 0.0) || !(s <= top))
+                return set_error(FD_ERR_OUT_OF_DOMAIN,
+                                 "fd_sparse_create: point %d coordinate %d = %g outside [%g, %g]", p, a, x,
+                                 g->origin[a], g->origin[a] + top * g->spacing[a]);
+            int64_t i = (int64_t)std::floor(s);
+            if (i > g->shape[a] - 2) i = g->shape[a] - 2;
+            frac[a] = s - (double)i;
+            lin += i * st[a];
+        }
+        base[p] = lin;
+        for (int k = 0; k < (1 << ndim); k++) {
+            double w = 1.0;
+            for (int a = 0; a < ndim; a++) w *= ((k >> a) & 1) ? frac[a] : 1.0 - frac[a];
+            weight[(size_t)p * 8 + k] = (float)w;
+        }
+    }
+    fd_sparse *sp = new (std::nothrow) fd_sparse();
+    if (!sp) return set_error(FD_ERR_NOMEM, "fd_sparse_create: out of host memory");
+    sp->g = *g;
+    sp->npoint = npoint;
+    sp->trace = (float *)dev_trace;
+    sp->nt = nt;
+    sp->stride = trace_stride;
+    sp->alloc_stream = (cudaStream_t)cuda_stream;
+    sp->d_base = nullptr;
+    sp->d_weight = nullptr;
+    if (npoint > 0) {
+        cudaStream_t s = sp->alloc_stream;
+        cudaError_t e = cudaMallocAsync((void **)&sp->d_base, sizeof(int64_t) * npoint, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&sp->d_weight, sizeof(float) * 8 * npoint, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sp->d_base, base.data(), sizeof(int64_t) * npoint, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sp->d_weight, weight.data(), sizeof(float) * 8 * npoint,
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            if (sp->d_base) cudaFreeAsync(sp->d_base, s);
+            if (sp->d_weight) cudaFreeAsync(sp->d_weight, s);
+            delete sp;
+            return e == cudaErrorMemoryAllocation ? set_error(FD_ERR_NOMEM, "fd_sparse_create: device allocation")
+                                                  : cuda_error(e, "fd_sparse_create");
+        }
+    }
+    SparseDev &d = sp->dev;
+    d.npoint = npoint;
+    d.ncorner = 1 << ndim;
+    d.base = sp->d_base;
+    d.weight = sp->d_weight;
+    for (int k = 0; k < 8; k++) {
+        int64_t off = 0;
+        if (k < d.ncorner)
+            for (int a = 0; a < ndim; a++) off += ((k >> a) & 1) * st[a];
+        d.corner_off[k] = off;
+    }
+    *out = sp;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_sparse_set_trace(fd_sparse *sp, void *dev_trace, int64_t nt, int64_t trace_stride)
+{
+    if (!sp) return set_error(FD_ERR_INVALID_ARG, "fd_sparse_set_trace: null handle");
+    if (sp->npoint > 0 && (!dev_trace || trace_stride < sp->npoint || nt < 0))
+        return set_error(FD_ERR_INVALID_ARG, "fd_sparse_set_trace: bad trace");
+    sp->trace = (float *)dev_trace;
+    sp->nt = nt;
+    sp->stride = trace_stride;
+    return FD_OK;
+}
+
+extern "C" void fd_sparse_destroy(fd_sparse *sp)
+{
+    if (!sp) return;
+    if (sp->d_base) cudaFreeAsync(sp->d_base, sp->alloc_stream);
+    if (sp->d_weight) cudaFreeAsync(sp->d_weight, sp->alloc_stream);
+    delete sp;
+}
+
+// ---------------------------------------------------------------------------
+// operator
+// ---------------------------------------------------------------------------
+
+static fd_status build_coef(fd_operator *op)
+{
+    double w[9];
+    fd_status s = fd_weights_central2(op->so, w);
+    if (s != FD_OK) return s;
+    const int M = op->so / 2;
+    const fd_grid &g = op->u->g;
+    Coef &cf = op->coef;
+    std::memset(&cf, 0, sizeof cf);
+    double centre = 0.0, lam = 0.0;
+    double smax = symbol_max(w, M);
+    for (int d = 0; d < g.ndim; d++) {
+        int a = 3 - g.ndim + d;
+        double h2 = g.spacing[d] * g.spacing[d];
+        for (int k = 1; k <= M; k++) cf.ax[a][k] = (float)(w[k] / h2);
+        cf.ax[a][0] = (float)(w[0] / h2);
+        centre += w[0] / h2;
+        lam += smax / h2;
+    }
+    cf.centre = (float)centre;
+    op->lambda_max = lam;
+    return FD_OK;
+}
+
+static fd_status reduce_m_min(fd_operator *op)
+{
+    unsigned int *d_bits = nullptr;
+    unsigned int init = 0x7f7fffffu;  // FLT_MAX
+    unsigned int bits = 0;
+    FD_CUDA(cudaMallocAsync((void **)&d_bits, sizeof(unsigned int), op->stream), "min(m): cudaMallocAsync");
+    cudaError_t e = cudaMemcpyAsync(d_bits, &init, sizeof init, cudaMemcpyHostToDevice, op->stream);
+    if (e == cudaSuccess) e = launch_min_reduce(op->geom, op->m->slot[0], d_bits, op->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, d_bits, sizeof bits, cudaMemcpyDeviceToHost, op->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->stream);
+    cudaFreeAsync(d_bits, op->stream);
+    if (e != cudaSuccess) return cuda_error(e, "min(m)");
+    op->launches += 1;
+    float mmin;
+    std::memcpy(&mmin, &bits, sizeof mmin);
+    op->m_min = (double)mmin;
+    if (!(op->m_min > 0.0)) return set_error(FD_ERR_INVALID_ARG, "fd_operator: m must be positive everywhere");
+    return FD_OK;
+}
+
+static void profile_clear(fd_operator *op)
+{
+    for (cudaEvent_t e : op->prof_ev) cudaEventDestroy(e);
+    op->prof_ev.clear();
+    op->prof_max = 0;
+    op->prof_used = 0;
+}
+
+// Record the start (which = 0) or stop (which = 1) event of a profiled launch.
+static cudaError_t profile_mark(fd_operator *op, int which)
+{
+    if (op->prof_used >= op->prof_max) return cudaSuccess;
+    cudaEvent_t e = op->prof_ev[(size_t)(2 * op->prof_used + which)];
+    cudaError_t r = cudaEventRecord(e, op->stream);
+    if (which == 1) op->prof_used += 1;
+    return r;
+}
+
+static void release(fd_operator *op)
+{
+    if (!op) return;
+    profile_clear(op);
+    if (op->c) cudaFreeAsync(op->c, op->stream);
+    if (op->d) cudaFreeAsync(op->d, op->stream);
+    if (op->status) cudaFreeAsync(op->status, op->stream);
+    tma_plan_release(op->tma);
+    delete op;
+}
+
+extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **out)
+{
+    if (!desc || !out) return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: null pointer");
+    *out = nullptr;
+    if (desc->kind != FD_DIFFUSION_EULER && desc->kind != FD_ACOUSTIC_LEAPFROG)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: unknown kind %d", desc->kind);
+    if (desc->space_order < 2 || desc->space_order > 16 || desc->space_order % 2)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: space order must be even, 2..16");
+    if (!desc->u || desc->u->levels != 2)
+        return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: u must be a 2-slot field");
+    const fd_grid &g = desc->u->g;
+    if (desc->kind == FD_ACOUSTIC_LEAPFROG) {
+        if (!desc->m || desc->m->levels != 1 || !same_shape(desc->m->g, g))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: acoustic needs a 1-slot m of u's shape");
+        if (desc->eta && (desc->eta->levels != 1 || !same_shape(desc->eta->g, g)))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: eta must be a 1-slot field of u's shape");
+        if ((desc->src && !same_shape(desc->src->g, g)) || (desc->rec && !same_shape(desc->rec->g, g)))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: sparse grid differs from u's");
+    } else {
+        if (!(desc->a > 0.0) || !std::isfinite(desc->a))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: diffusivity a must be > 0");
+        if (desc->flags & FD_FLAG_REVERSE)
+            return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: diffusion has no reverse mode");
+    }
+    fd_operator *op = new (std::nothrow) fd_operator();
+    if (!op) return set_error(FD_ERR_NOMEM, "fd_operator_create: out of host memory");
+    op->kind = desc->kind;
+    op->so = desc->space_order;
+    op->u = desc->u;
+    op->m = desc->m;
+    op->eta = desc->eta;
+    op->a = desc->a;
+    op->src = desc->kind == FD_ACOUSTIC_LEAPFROG ? desc->src : nullptr;
+    op->rec = desc->kind == FD_ACOUSTIC_LEAPFROG ? desc->rec : nullptr;
+    op->stream = (cudaStream_t)desc->cuda_stream;
+    op->flags = desc->flags;
+    op->geom = geom_of(g);
+    op->c = op->d = nullptr;
+    op->status = nullptr;
+    op->coef_dt = -1.0;
+    op->m_min = 0.0;
+    op->launches = 0;
+    op->prof_max = 0;
+    op->prof_used = 0;
+    fd_status s = build_coef(op);
+    if (s != FD_OK) { release(op); return s; }
+    cudaError_t e = cudaMallocAsync((void **)&op->status, sizeof(int), op->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(op->status, 0, sizeof(int), op->stream);
+    if (e != cudaSuccess) { release(op); return cuda_error(e, "fd_operator_create: status word"); }
+    if (op->kind == FD_ACOUSTIC_LEAPFROG) {
+        size_t bytes = sizeof(float) * (size_t)slot_elems(g);
+        e = cudaMallocAsync((void **)&op->c, bytes, op->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&op->d, bytes, op->stream);
+        if (e != cudaSuccess) {
+            release(op);
+            return e == cudaErrorMemoryAllocation ? set_error(FD_ERR_NOMEM, "fd_operator_create: coefficient fields")
+                                                  : cuda_error(e, "fd_operator_create");
+        }
+        s = reduce_m_min(op);
+        if (s != FD_OK) { release(op); return s; }
+    }
+    s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+    if (s != FD_OK) { release(op); return s; }
+    *out = op;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_bind(fd_operator *op, const char *name, void *obj)
+{
+    if (!op || !name) return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: null pointer");
+    const fd_grid &g = op->u->g;
+    std::string n(name);
+    if (n == "u") {
+        fd_field *f = (fd_field *)obj;
+        if (!f || f->levels != 2 || !same_shape(f->g, g))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: u must be a 2-slot field of the same shape");
+        op->u = f;
+        return tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+    }
+    if (n == "m" || n == "eta") {
+        if (op->kind != FD_ACOUSTIC_LEAPFROG)
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: %s only for the acoustic operator", name);
+        fd_field *f = (fd_field *)obj;
+        if ((n == "m" && !f) || (f && (f->levels != 1 || !same_shape(f->g, g))))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: %s must be a 1-slot field of u's shape", name);
+        if (n == "m") {
+            op->m = f;
+            fd_status s = reduce_m_min(op);
+            if (s != FD_OK) return s;
+        } else {
+            op->eta = f;
+        }
+        op->coef_dt = -1.0;
+        return FD_OK;
+    }
+    if (n == "src" || n == "rec") {
+        fd_sparse *sp = (fd_sparse *)obj;
+        if (sp && !same_shape(sp->g, g)) return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: sparse grid differs");
+        if (op->kind != FD_ACOUSTIC_LEAPFROG && sp)
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: sparse points only for the acoustic operator");
+        (n == "src" ? op->src : op->rec) = sp;
+        return FD_OK;
+    }
+    if (n == "stream") {
+        op->stream = (cudaStream_t)obj;
+        return FD_OK;
+    }
+    if (n == "a") {
+        const double *a = (const double *)obj;
+        if (!a || !(*a > 0.0)) return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: a must be > 0");
+        op->a = *a;
+        return FD_OK;
+    }
+    return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: unknown name '%s'", name);
+}
+
+extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt)
+{
+    if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: null operator");
+    if (nt < 0 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: need t0 >= 0, nt >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: dt must be > 0");
+    const bool reverse = (op->flags & FD_FLAG_REVERSE) != 0;
+    for (fd_sparse *sp : {op->src, op->rec})
+        if (sp && sp->npoint > 0 && t0 + nt > sp->nt)
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: trace has %lld rows, need %lld",
+                             (long long)sp->nt, (long long)(t0 + nt));
+    if (!(op->flags & FD_FLAG_NO_CFL_CHECK)) {
+        if (op->kind == FD_ACOUSTIC_LEAPFROG) {
+            double limit = 2.0 * std::sqrt(op->m_min / op->lambda_max);
+            if (dt > limit)
+                return set_error(FD_ERR_UNSTABLE, "fd_operator_apply: dt = %g above the stability limit %g", dt, limit);
+        } else {
+            double limit = 2.0 / (op->a * op->lambda_max);
+            if (dt > limit)
+                return set_error(FD_ERR_UNSTABLE, "fd_operator_apply: a*dt = %g above the Euler limit %g", op->a * dt,
+                                 op->a * limit);
+        }
+    }
+    if (nt == 0) return FD_OK;
+    const int M = op->so / 2;
+    const Geom &g = op->geom;
+    cudaStream_t st = op->stream;
+    const bool plain = (op->flags & FD_FLAG_PLAIN_KERNELS) != 0 || !op->tma.ready;
+    if (op->kind == FD_ACOUSTIC_LEAPFROG) {
+        if (op->coef_dt != dt) {
+            FD_CUDA(launch_coefficients(g, op->m->slot[0], op->eta ? op->eta->slot[0] : nullptr, dt, op->c, op->d, st),
+                    "coefficients");
+            op->launches += 1;
+            op->coef_dt = dt;
+        }
+        for (int64_t q = 0; q < nt; q++) {
+            int64_t n = reverse ? t0 + nt - 1 - q : t0 + q;
+            int cur = (int)((reverse ? n + 1 : n) & 1);
+            float *u = op->u->slot[cur];
+            float *up = op->u->slot[cur ^ 1];
+            if (op->rec && op->rec->npoint > 0) {
+                FD_CUDA(launch_interpolate(op->rec->dev, u, op->rec->trace + n * op->rec->stride, st), "interpolate");
+                op->launches += 1;
+            }
+            FD_CUDA(profile_mark(op, 0), "profile");
+            if (plain) {
+                FD_CUDA(launch_acoustic_plain(M, g, op->coef, u, up, op->c, op->d, st), "acoustic step");
+            } else {
+                FD_CUDA(launch_acoustic_tma(op->tma, M, g, op->coef, cur, op->status, st), "acoustic step");
+            }
+            FD_CUDA(profile_mark(op, 1), "profile");
+            op->launches += 1;
+            if (op->src && op->src->npoint > 0) {
+                FD_CUDA(launch_inject(op->src->dev, op->c, op->src->trace + n * op->src->stride, up, st), "inject");
+                op->launches += 1;
+            }
+        }
+    } else {
+        const float adt = (float)(op->a * dt);
+        for (int64_t q = 0; q < nt; q++) {
+            int64_t n = t0 + q;
+            int cur = (int)(n & 1);
+            FD_CUDA(profile_mark(op, 0), "profile");
+            FD_CUDA(launch_diffusion_plain(M, g, op->coef, adt, op->u->slot[cur], op->u->slot[cur ^ 1], st),
+                    "diffusion step");
+            FD_CUDA(profile_mark(op, 1), "profile");
+            op->launches += 1;
+        }
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_sync(fd_operator *op)
+{
+    if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_sync: null operator");
+    FD_CUDA(cudaStreamSynchronize(op->stream), "fd_operator_sync");
+    FD_CUDA(cudaGetLastError(), "fd_operator_sync");
+    int status = 0;
+    FD_CUDA(cudaMemcpy(&status, op->status, sizeof status, cudaMemcpyDeviceToHost), "fd_operator_sync: status");
+    if (status != 0) {
+        cudaMemset(op->status, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        return set_error(FD_ERR_TIMEOUT, "fd_operator_sync: a device wait gave up (code %d)", status);
+    }
+    return FD_OK;
+}
+
+extern "C" void fd_operator_destroy(fd_operator *op) { release(op); }
+
+extern "C" int64_t fd_operator_launch_count(const fd_operator *op) { return op ? op->launches : 0; }
+
+extern "C" fd_status fd_operator_profile(fd_operator *op, int64_t max_launches)
+{
+    if (!op || max_launches < 0 || max_launches > (int64_t(1) << 20))
+        return set_error(FD_ERR_INVALID_ARG, "fd_operator_profile: bad arguments");
+    FD_CUDA(cudaStreamSynchronize(op->stream), "fd_operator_profile");
+    profile_clear(op);
+    try {
+        op->prof_ev.resize((size_t)(2 * max_launches), nullptr);
+    } catch (...) {
+        return set_error(FD_ERR_NOMEM, "fd_operator_profile: out of host memory");
+    }
+    for (auto &e : op->prof_ev) {
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            e = nullptr;
+            profile_clear(op);
+            return cuda_error(r, "fd_operator_profile: cudaEventCreate");
+        }
+    }
+    op->prof_max = max_launches;
+    op->prof_used = 0;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_profile_read(fd_operator *op, double *total_ms, int64_t *launches)
+{
+    if (!op || !total_ms || !launches) return set_error(FD_ERR_INVALID_ARG, "fd_operator_profile_read: null pointer");
+    FD_CUDA(cudaStreamSynchronize(op->stream), "fd_operator_profile_read");
+    double sum = 0.0;
+    for (int64_t i = 0; i < op->prof_used; i++) {
+        float ms = 0.0f;
+        FD_CUDA(cudaEventElapsedTime(&ms, op->prof_ev[(size_t)(2 * i)], op->prof_ev[(size_t)(2 * i + 1)]),
+                "fd_operator_profile_read");
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = op->prof_used;
+    return FD_OK;
+}

@@ -1,0 +1,56 @@
+// Internal types shared by the host API (fd_api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fd.h"
+
+namespace fdgb {
+
+constexpr int kMaxHalfWidth = 8;  // SO <= 16
+
+// Three-axis view of a grid: a 2D grid (n0, n1) is the single plane
+// (1, n0, n1) with the plane axis not differentiated.  Axis 2 is contiguous.
+struct Geom {
+    int ndim;          // 2 or 3
+    int64_t n[3];      // interior extents in the 3-axis view
+    int64_t s0, s1;    // strides (elements) of axes 0 and 1; axis 2 stride is 1
+};
+
+// FD coefficients of one operator: coef[a][k] = w_k / h_a^2 (FP64 -> FP32
+// once), axis a in the 3-axis view (coef[0] all zero for 2D grids), and the
+// summed centre weight centre = sum_a w_0 / h_a^2.
+struct Coef {
+    float centre;
+    float ax[3][kMaxHalfWidth + 1];
+};
+
+// Linear-interpolation table of a sparse object on the device.
+struct SparseDev {
+    int npoint;
+    int ncorner;             // 4 (2D) or 8 (3D)
+    const int64_t *base;     // [npoint] linear index of the lowest corner
+    const float *weight;     // [npoint][8]
+    int64_t corner_off[8];   // linear offset of corner k from base
+};
+
+// ---- launchers (kernel files) -------------------------------------------
+
+cudaError_t launch_coefficients(const Geom &g, const float *m, const float *eta, double dt,
+                                float *c, float *d, cudaStream_t st);
+cudaError_t launch_min_reduce(const Geom &g, const float *m, unsigned int *out_bits,
+                              cudaStream_t st);
+cudaError_t launch_interpolate(const SparseDev &sp, const float *u, float *out_row,
+                               cudaStream_t st);
+cudaError_t launch_inject(const SparseDev &sp, const float *c, const float *row, float *u,
+                          cudaStream_t st);
+
+// plain kernels: one thread per (d1, d2) column, streaming d0
+cudaError_t launch_acoustic_plain(int half_width, const Geom &g, const Coef &cf,
+                                  const float *u, float *u_prev_out, const float *c,
+                                  const float *d, cudaStream_t st);
+cudaError_t launch_diffusion_plain(int half_width, const Geom &g, const Coef &cf, float adt,
+                                   const float *u, float *u_out, cudaStream_t st);
+
+}  // namespace fdgb

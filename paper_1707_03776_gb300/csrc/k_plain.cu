@@ -1,0 +1,233 @@
+// Plain CUDA kernels: coefficient preparation, sparse interpolation and
+// injection, and the one-thread-per-column stencil updates.
+//
+// The stencil kernels here are the straightforward form of the update: each
+// thread owns one (d1, d2) column and walks d0, reading every neighbour from
+// global memory (L1/L2 catch the reuse).  The zero halo is an index test.
+#include "fd_internal.h"
+
+namespace fdgb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// c = dt^2/m and d = dt*eta/m at every interior node (Seismic Inversion
+// Example: the coefficients of u(t+dt) after solving the discretised
+// m u_tt + eta u_t - lap u = q).  eta may be null (d = 0).
+__global__ void coefficients_kernel(Geom g, const float *__restrict__ m,
+                                    const float *__restrict__ eta, float dt2, float dt,
+                                    float *__restrict__ c, float *__restrict__ d)
+{
+    const int64_t rows = g.n[0] * g.n[1];
+    const int64_t total = rows * g.n[2];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = q / g.n[2];
+        int64_t i2 = q - row * g.n[2];
+        int64_t i0 = row / g.n[1];
+        int64_t i1 = row - i0 * g.n[1];
+        int64_t at = i0 * g.s0 + i1 * g.s1 + i2;
+        float mv = m[at];
+        c[at] = dt2 / mv;
+        d[at] = eta ? dt * eta[at] / mv : 0.0f;
+    }
+}
+
+// min over the interior of a positive field, as the order-preserving bit
+// pattern of a non-negative float.
+__global__ void min_reduce_kernel(Geom g, const float *__restrict__ m, unsigned int *out)
+{
+    const int64_t total = g.n[0] * g.n[1] * g.n[2];
+    float v = 3.0e38f;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = q / g.n[2];
+        int64_t i2 = q - row * g.n[2];
+        int64_t i0 = row / g.n[1];
+        int64_t i1 = row - i0 * g.n[1];
+        float x = m[i0 * g.s0 + i1 * g.s1 + i2];
+        // a non-positive or NaN entry poisons the minimum to 0
+        v = (x > 0.0f) ? fminf(v, x) : 0.0f;
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(out, __float_as_uint(v));
+}
+
+// rec[p] = sum_k w_pk u(base_p + off_k)  (rec.interpolate(expr=u))
+__global__ void interpolate_kernel(SparseDev sp, const float *__restrict__ u,
+                                   float *__restrict__ out)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sp.npoint) return;
+    const int64_t b = sp.base[p];
+    const float *w = sp.weight + (int64_t)p * 8;
+    float s = 0.0f;
+    for (int k = 0; k < sp.ncorner; k++) s = fmaf(w[k], u[b + sp.corner_off[k]], s);
+    out[p] = s;
+}
+
+// u(base_p + off_k) += w_pk * c(node) * src[p]  (src.inject(u, src*dt^2/m));
+// atomics because several points may share a node.
+__global__ void inject_kernel(SparseDev sp, const float *__restrict__ c,
+                              const float *__restrict__ row, float *u)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    int p = q / sp.ncorner;
+    int k = q - p * sp.ncorner;
+    if (p >= sp.npoint) return;
+    int64_t at = sp.base[p] + sp.corner_off[k];
+    float w = sp.weight[(int64_t)p * 8 + k];
+    atomicAdd(u + at, w * c[at] * row[p]);
+}
+
+// Zero-halo load along one axis.
+__device__ __forceinline__ float ld0(const float *__restrict__ u, int64_t at, int64_t i,
+                                     int64_t n)
+{
+    return (i >= 0 && i < n) ? u[at] : 0.0f;
+}
+
+// Laplacian at (i0, i1, i2): centre * u + sum_a sum_k coef[a][k] (u[-k] + u[+k]).
+template <int M, bool THREE_D>
+__device__ __forceinline__ float laplacian_at(const Geom &g, const Coef &cf,
+                                              const float *__restrict__ u, int64_t at,
+                                              int64_t i0, int64_t i1, int64_t i2)
+{
+    float lap = cf.centre * u[at];
+#pragma unroll
+    for (int k = 1; k <= M; k++) {
+        float s2 = ld0(u, at - k, i2 - k, g.n[2]) + ld0(u, at + k, i2 + k, g.n[2]);
+        float s1 = ld0(u, at - k * g.s1, i1 - k, g.n[1]) + ld0(u, at + k * g.s1, i1 + k, g.n[1]);
+        lap = fmaf(cf.ax[2][k], s2, lap);
+        lap = fmaf(cf.ax[1][k], s1, lap);
+        if (THREE_D) {
+            float s0 = ld0(u, at - k * g.s0, i0 - k, g.n[0]) + ld0(u, at + k * g.s0, i0 + k, g.n[0]);
+            lap = fmaf(cf.ax[0][k], s0, lap);
+        }
+    }
+    return lap;
+}
+
+// Acoustic leapfrog, in place over the previous slot:
+//   u_prev <- 2u - u_prev + c L u - d (u - u_prev)
+template <int M, bool THREE_D>
+__global__ void acoustic_plain_kernel(Geom g, Coef cf, const float *__restrict__ u,
+                                      float *__restrict__ up, const float *__restrict__ c,
+                                      const float *__restrict__ d)
+{
+    int64_t i2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t i1 = blockIdx.y;
+    if (i2 >= g.n[2]) return;
+    for (int64_t i0 = 0; i0 < g.n[0]; i0++) {
+        int64_t at = i0 * g.s0 + i1 * g.s1 + i2;
+        float lap = laplacian_at<M, THREE_D>(g, cf, u, at, i0, i1, i2);
+        float uc = u[at];
+        float upv = up[at];
+        up[at] = 2.0f * uc - upv + c[at] * lap - d[at] * (uc - upv);
+    }
+}
+
+// Explicit Euler diffusion: u_out <- u + a dt L u
+template <int M, bool THREE_D>
+__global__ void diffusion_plain_kernel(Geom g, Coef cf, float adt, const float *__restrict__ u,
+                                       float *__restrict__ out)
+{
+    int64_t i2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t i1 = blockIdx.y;
+    if (i2 >= g.n[2]) return;
+    for (int64_t i0 = 0; i0 < g.n[0]; i0++) {
+        int64_t at = i0 * g.s0 + i1 * g.s1 + i2;
+        float lap = laplacian_at<M, THREE_D>(g, cf, u, at, i0, i1, i2);
+        out[at] = fmaf(adt, lap, u[at]);
+    }
+}
+
+int grid_stride_blocks(int64_t total)
+{
+    int64_t b = (total + kThreads - 1) / kThreads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_coefficients(const Geom &g, const float *m, const float *eta, double dt,
+                                float *c, float *d, cudaStream_t st)
+{
+    int64_t total = g.n[0] * g.n[1] * g.n[2];
+    coefficients_kernel<<<grid_stride_blocks(total), kThreads, 0, st>>>(
+        g, m, eta, (float)(dt * dt), (float)dt, c, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_min_reduce(const Geom &g, const float *m, unsigned int *out_bits,
+                              cudaStream_t st)
+{
+    int64_t total = g.n[0] * g.n[1] * g.n[2];
+    min_reduce_kernel<<<grid_stride_blocks(total), kThreads, 0, st>>>(g, m, out_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(const SparseDev &sp, const float *u, float *out_row,
+                               cudaStream_t st)
+{
+    if (sp.npoint <= 0) return cudaSuccess;
+    interpolate_kernel<<<(sp.npoint + 127) / 128, 128, 0, st>>>(sp, u, out_row);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const SparseDev &sp, const float *c, const float *row, float *u,
+                          cudaStream_t st)
+{
+    if (sp.npoint <= 0) return cudaSuccess;
+    int total = sp.npoint * sp.ncorner;
+    inject_kernel<<<(total + 127) / 128, 128, 0, st>>>(sp, c, row, u);
+    return cudaGetLastError();
+}
+
+#define FD_FOR_EACH_M(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
+
+cudaError_t launch_acoustic_plain(int M, const Geom &g, const Coef &cf, const float *u,
+                                  float *up, const float *c, const float *d, cudaStream_t st)
+{
+    dim3 grid((unsigned)((g.n[2] + 127) / 128), (unsigned)g.n[1]);
+    bool three = g.ndim == 3;
+    switch (M) {
+#define CASE(MM)                                                                          \
+    case MM:                                                                              \
+        if (three)                                                                        \
+            acoustic_plain_kernel<MM, true><<<grid, 128, 0, st>>>(g, cf, u, up, c, d);    \
+        else                                                                              \
+            acoustic_plain_kernel<MM, false><<<grid, 128, 0, st>>>(g, cf, u, up, c, d);   \
+        break;
+        FD_FOR_EACH_M(CASE)
+#undef CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diffusion_plain(int M, const Geom &g, const Coef &cf, float adt,
+                                   const float *u, float *out, cudaStream_t st)
+{
+    dim3 grid((unsigned)((g.n[2] + 127) / 128), (unsigned)g.n[1]);
+    bool three = g.ndim == 3;
+    switch (M) {
+#define CASE(MM)                                                                          \
+    case MM:                                                                              \
+        if (three)                                                                        \
+            diffusion_plain_kernel<MM, true><<<grid, 128, 0, st>>>(g, cf, adt, u, out);   \
+        else                                                                              \
+            diffusion_plain_kernel<MM, false><<<grid, 128, 0, st>>>(g, cf, adt, u, out);  \
+        break;
+        FD_FOR_EACH_M(CASE)
+#undef CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fdgb
