@@ -14,7 +14,8 @@ Inputs defined here (the readings of the paper's unspecified `Model(...)`):
   * damping eta = m * sigma with the polynomial sponge
     sigma(x) = sum_axes sigma_max (r/W)^2 on the W cells next to every face
     (r in (0, W] cells into the layer), sigma_max = 3 v_max ln(1/R) / (2 W h),
-    R = 1e-3; so that dt*eta/m = dt*sigma;
+    R = 1e-3, W = 40 (thinner layers of scaled-down grids keep the 40-cell
+    sigma_max); so that dt*eta/m = dt*sigma;
   * source: Ricker wavelet (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2);
   * diffusion: indicator of the ring 0.25 < r < 0.35 about (0.5, 0.5).
 """
@@ -48,8 +49,13 @@ def two_layer_velocity(shape, v_top=1500.0, v_bottom=2500.0, interface=None) -> 
     return v
 
 
-def sponge_sigma(shape, spacing, width, v_max, reflection=1e-3) -> np.ndarray:
-    """Polynomial sponge damping rate sigma (1/s, FP64) on every face."""
+def sponge_sigma(shape, spacing, width, v_max, reflection=1e-3, ref_width=None) -> np.ndarray:
+    """Polynomial sponge damping rate sigma (1/s, FP64) on every face.
+
+    sigma_max uses `ref_width` cells (default: the layer width); scaled-down
+    test grids keep the 40-cell strength so that dt*sigma stays ~0.1 per axis
+    (a thin layer with its own sigma_max would push dt*sigma past 1, where the
+    explicit damped update is unstable)."""
     sigma = np.zeros(shape, dtype=np.float64)
     if width <= 0:
         return sigma
@@ -59,7 +65,8 @@ def sponge_sigma(shape, spacing, width, v_max, reflection=1e-3) -> np.ndarray:
         h = spacing[a]
         i = np.arange(n, dtype=np.float64)
         r = np.maximum(0.0, np.maximum(width - i, i - (n - 1 - width)))
-        smax = 3.0 * v_max * math.log(1.0 / reflection) / (2.0 * width * h)
+        wref = width if ref_width is None else ref_width
+        smax = 3.0 * v_max * math.log(1.0 / reflection) / (2.0 * wref * h)
         prof = smax * (r / width) ** 2
         sh = [1] * ndim
         sh[a] = n
@@ -85,7 +92,7 @@ def acoustic_config(n=512, space_order=8, nt=1000, h=10.0, sponge=40, nrec_side=
     dt = cfl * h / v_max
     m64 = 1.0 / v ** 2
     m = m64.astype(np.float32)
-    sigma = sponge_sigma(shape, spacing, sponge, v_max)
+    sigma = sponge_sigma(shape, spacing, sponge, v_max, ref_width=max(sponge, 40))
     eta = (m.astype(np.float64) * sigma).astype(np.float32)
     depth = float(sponge)
     centre = (n - 1) / 2.0

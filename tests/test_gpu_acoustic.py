@@ -23,7 +23,7 @@ TRACE_TOL = 1e-4
 def _model(shape, h, sponge, seed):
     v = wl.two_layer_velocity(shape, 1500.0, 2500.0)
     m = (1.0 / v ** 2).astype(np.float32)
-    sig = wl.sponge_sigma(shape, (h,) * len(shape), sponge, 2500.0)
+    sig = wl.sponge_sigma(shape, (h,) * len(shape), sponge, 2500.0, ref_width=40)
     eta = (m.astype(np.float64) * sig).astype(np.float32)
     return m, eta, 0.4 * h / 2500.0
 

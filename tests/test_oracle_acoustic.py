@@ -212,7 +212,7 @@ def _adjoint_case(ndim, so, n, nt, seed):
     origin = (0.0,) * ndim
     v = wl.two_layer_velocity(shape, 1500.0, 2500.0)
     m = (1.0 / v ** 2).astype(np.float32)
-    sig = wl.sponge_sigma(shape, h, 4, 2500.0)
+    sig = wl.sponge_sigma(shape, h, 4, 2500.0, ref_width=40)
     eta = (m.astype(np.float64) * sig).astype(np.float32)
     dt = 0.4 * 10.0 / 2500.0
     src_c = wl.random_points(shape, h, origin, 3, seed)
