@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=3, help="time steps in the CPU-oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-rows", action="store_true", help="skip the secondary rows (2D diffusion)")
     p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
     return p.parse_args()
 
@@ -198,6 +199,44 @@ def kernel_traffic(so):
     return None
 
 
+def bench_diffusion(steps=5, warmup=3):
+    """The 2D diffusion row (256^2 ring, 500 explicit Euler steps), timed
+    with CUDA events: the grid is L2/shared-memory resident, so it is reported
+    as time per step, not against the HBM roofline."""
+    import torch
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    cfg = wl.diffusion_ring()
+    grid = fd.Grid(cfg["shape"], cfg["spacing"], cfg["origin"])
+    u = fd.TimeData("u", grid)
+    u0 = torch.from_numpy(cfg["u0"]).cuda()
+    op = fd.Operator(fd.FD_DIFFUSION_EULER, 2, u, a=cfg["a"])
+    stream = torch.cuda.current_stream()
+
+    def run():
+        u.at(0).copy_(u0)
+        op.apply(0, cfg["nt"], cfg["dt"])
+
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    n0 = op.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    op.sync()
+    ms = e0.elapsed_time(e1) / steps
+    pts = float(cfg["shape"][0] * cfg["shape"][1]) * cfg["nt"]
+    return {"workload": "diffusion2d_256^2_ring_so2_nt500", "value": pts / (ms * 1e-3) / 1e9, "unit": "GPts/s",
+            "ms_per_run": ms, "us_per_time_step": 1e3 * ms / cfg["nt"],
+            "launches_per_run": (op.launches - n0) / steps,
+            "bound": "latency (grid held in one cluster's shared memory)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -307,12 +346,16 @@ def run_ours(args):
                "sample": "%d of %d time steps of the same %d^3 SO%d forward run, FP32 loop nest, %.1f s" % (
                    args.cpu_steps, args.nt, args.n, args.so, el)}
 
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = {"diffusion": bench_diffusion()}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(args), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "rows": rows,
                 "device": torch.cuda.get_device_name(local)}
         print(json.dumps(line), flush=True)
     if world > 1:

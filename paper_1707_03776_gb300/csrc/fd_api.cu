@@ -15,13 +15,6 @@
 #include "fd_internal_host.h"
 #include "fd_tma.h"
 
-struct fd_grid {
-    int ndim;
-    int64_t shape[3];
-    double spacing[3];
-    double origin[3];
-};
-
 struct fd_field {
     fd_grid g;
     int levels;
@@ -57,6 +50,9 @@ struct fd_operator {
     double m_min;          // min(m) over the grid
     int64_t launches;
     fdgb::TmaPlan tma;     // tiled-kernel plan (tensor maps, tiling)
+    bool cluster_ok;       // diffusion: whole run in one cluster launch
+    int cluster_n;
+    size_t cluster_smem;
     // stencil-kernel timing (fd_operator_profile)
     std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
     int64_t prof_max;
@@ -506,6 +502,8 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     }
     s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
     if (s != FD_OK) { release(op); return s; }
+    op->cluster_ok = op->kind == FD_DIFFUSION_EULER &&
+                     diffusion_cluster_fits(op->so / 2, op->geom, &op->cluster_n, &op->cluster_smem);
     *out = op;
     return FD_OK;
 }
@@ -614,6 +612,23 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                 FD_CUDA(launch_inject(op->src->dev, op->c, op->src->trace + n * op->src->stride, up, st), "inject");
                 op->launches += 1;
             }
+        }
+    } else if (op->cluster_ok && !(op->flags & FD_FLAG_PLAIN_KERNELS)) {
+        const float adt = (float)(op->a * dt);
+        int64_t done = 0;
+        while (done < nt) {
+            const int64_t chunk = (nt - done) < (int64_t(1) << 30) ? (nt - done) : (int64_t(1) << 30);
+            const int64_t t = t0 + done;
+            float *u0 = op->u->slot[t & 1];
+            float *last = op->u->slot[(t + chunk) & 1];
+            float *prev = chunk >= 2 ? op->u->slot[(t + chunk - 1) & 1] : nullptr;
+            FD_CUDA(profile_mark(op, 0), "profile");
+            FD_CUDA(launch_diffusion_cluster(M, g, op->coef, adt, u0, last, prev, (int)chunk, op->cluster_n,
+                                             op->cluster_smem, st),
+                    "diffusion cluster run");
+            FD_CUDA(profile_mark(op, 1), "profile");
+            op->launches += 1;
+            done += chunk;
         }
     } else {
         const float adt = (float)(op->a * dt);

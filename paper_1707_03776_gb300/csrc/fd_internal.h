@@ -53,4 +53,11 @@ cudaError_t launch_acoustic_plain(int half_width, const Geom &g, const Coef &cf,
 cudaError_t launch_diffusion_plain(int half_width, const Geom &g, const Coef &cf, float adt,
                                    const float *u, float *u_out, cudaStream_t st);
 
+// whole-run diffusion in one thread-block cluster (2D grids that fit in the
+// cluster's shared memory)
+bool diffusion_cluster_fits(int half_width, const Geom &g, int *nclusters, size_t *smem);
+cudaError_t launch_diffusion_cluster(int half_width, const Geom &g, const Coef &cf, float adt,
+                                     const float *u0, float *out_last, float *out_prev, int nt,
+                                     int nclusters, size_t smem, cudaStream_t st);
+
 }  // namespace fdgb

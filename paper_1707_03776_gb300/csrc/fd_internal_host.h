@@ -1,7 +1,17 @@
 // Host-side helpers shared by the C-ABI translation units.
 #pragma once
 
+#include <stdint.h>
+
 #include "fd.h"
+
+// The grid handle behind fd_grid*.
+struct fd_grid {
+    int ndim;
+    int64_t shape[3];
+    double spacing[3];
+    double origin[3];
+};
 
 namespace fdgb {
 
