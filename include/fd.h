@@ -259,6 +259,38 @@ int64_t fd_operator_launch_count(const fd_operator *op);
 fd_status fd_operator_profile(fd_operator *op, int64_t max_launches);
 fd_status fd_operator_profile_read(fd_operator *op, double *total_ms, int64_t *launches);
 
+/* ------------------------------------------------------------------------
+ * Interpolation without allocation (the paper has no counterpart)
+ * ------------------------------------------------------------------------ */
+
+/* Largest point count fd_interpolate_noalloc accepts. */
+#define FD_NOALLOC_MAX_POINTS 65536
+
+/* Record a field at off-grid points without allocating any memory: for
+ * callers that cannot call cudaMalloc when they record -- device memory fully
+ * reserved up front by another allocator's pool, a fixed memory budget set at
+ * start-up, or a loop that must not risk the device-wide synchronisation an
+ * allocation or free can cause.  out[p] = sum of the 2^ndim linear weights of
+ * point p times the field at the surrounding nodes, the same table and kernel
+ * as the `rec` interpolation of fd_operator_apply.
+ *   grid       grid the field belongs to
+ *   coords     host FP64 [npoint][ndim], physical units, inside the grid
+ *   dev_field  device FP32, one slot in the layout of fd_field_layout
+ *   dev_out    device FP32 [npoint]
+ *   cuda_stream  cudaStream_t the copy and the kernel are enqueued on
+ * The interpolation table lives in one static device array of
+ * FD_NOALLOC_MAX_POINTS entries (40 bytes each, 2.6 MB) that every GPU loading
+ * the library holds until the process exits; the call writes the entries it
+ * uses (nothing in it needs to start at zero) and calls no allocating
+ * routine.  All calls on a device share that array and it keeps the last
+ * call's table: calls whose work overlaps on the GPU (e.g. on two streams)
+ * race.  The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Errors: FD_ERR_INVALID_ARG (npoint > FD_NOALLOC_MAX_POINTS or < 0, null
+ * pointers), FD_ERR_OUT_OF_DOMAIN, FD_ERR_CUDA. */
+fd_status fd_interpolate_noalloc(const fd_grid *grid, int npoint, const double *coords,
+                                 const void *dev_field, void *dev_out, void *cuda_stream);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

@@ -74,7 +74,10 @@ _SIGNATURES = [
     ("fd_operator_launch_count", ctypes.c_int64, [_vp]),
     ("fd_operator_profile", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("fd_operator_profile_read", ctypes.c_int, [_vp, _c_f64p, _c_i64p]),
+    ("fd_interpolate_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _c_f64p, _vp, _vp, _vp]),
 ]
+
+FD_NOALLOC_MAX_POINTS = 65536
 
 EXPORTED = [s[0] for s in _SIGNATURES]
 
@@ -239,6 +242,15 @@ def fd_operator_profile_read(op):
     n = ctypes.c_int64(0)
     _check(lib().fd_operator_profile_read(op, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def fd_interpolate_noalloc(grid, coords, dev_field, dev_out, stream=0):
+    """Interpolate a device field slot at host coordinates into dev_out
+    without any allocation (see include/fd.h)."""
+    c = _f64(coords)
+    npoint = c.shape[0] if c.ndim > 1 else 0
+    _check(lib().fd_interpolate_noalloc(grid, npoint, c.ctypes.data_as(_c_f64p) if npoint else None,
+                                        int(dev_field) or None, int(dev_out) or None, int(stream) or None))
 
 
 # --------------------------------------------------------------------------
