@@ -250,6 +250,53 @@ void fd_operator_destroy(fd_operator *op);
  * it was created (for launch accounting). */
 int64_t fd_operator_launch_count(const fd_operator *op);
 
+/* One time step between caller buffers, for schemes that keep more than two
+ * states (the checkpoint recomputation of the adjoint-state gradient): the
+ * update of fd_operator_apply's step n (including the operator's receiver
+ * interpolation into rec[n] and source injection from src[n]) reading
+ * u_cur (u^n; with FD_FLAG_REVERSE the state of time n+1) and u_prev (u^{n-1};
+ * reverse: time n+2) and writing u_next (u^{n+1}; reverse: time n).  All three
+ * are device FP32 slots in the layout of fd_field_layout, 32-byte aligned;
+ * u_next may equal u_prev (in place) but not u_cur.  Acoustic operators only.
+ * Errors: as fd_operator_apply, plus FD_ERR_LAYOUT for misaligned buffers. */
+fd_status fd_operator_step(fd_operator *op, int64_t n, double dt, const void *u_cur,
+                           const void *u_prev, void *u_next);
+
+/* Imaging condition of the adjoint-state gradient with respect to m:
+ * grad += scale * mu * (u0 - 2 u1 + u2) at every interior node, with mu the
+ * adjoint state of time n and u0, u1, u2 the forward states of times n, n-1,
+ * n-2 (device FP32 slots of `grid`'s layout, 16-byte aligned).  For
+ * J(m) = 1/2 |R u - d|^2, whose adjoint is the reverse run with the residual
+ * injected at the receivers, dJ/dm = -(1/dt^2) sum_n mu^n (u^n - 2u^{n-1} +
+ * u^{n-2}), so scale = -1/dt^2 (an extension of the paper's adjoint operator
+ * to the gradient it is built for).  Enqueued on cuda_stream.
+ * Errors: FD_ERR_INVALID_ARG, FD_ERR_LAYOUT, FD_ERR_CUDA. */
+fd_status fd_imaging_accumulate(const fd_grid *grid, double scale, const void *mu, const void *u0,
+                                const void *u1, const void *u2, void *grad, void *cuda_stream);
+
+/* Tiling of the operator's tiled grid-update kernel (3D acoustic): tiles of
+ * at most `rows` rows of d1 by 64 columns of d2, swept along d0, with
+ * `stages` planes prefetched (2..4).  0 keeps the planner's choice for that
+ * parameter.  Used by the autotuner, which times candidates and keeps the
+ * fastest (the GPU analogue of the paper's block-size auto-tuning, Automated
+ * code generation section).  Errors: FD_ERR_UNSUPPORTED when the tiling does
+ * not fit in shared memory or the operator has no tiled kernel (the previous
+ * tiling is kept), FD_ERR_INVALID_ARG. */
+fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stages);
+/* The tiling in use: rows per tile, prefetch depth, CTAs per launch (all 0
+ * when the operator runs the plain kernels). */
+fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, int *stages, int *ctas);
+
+/* Autotuner: time candidate tilings (tile heights 8..32 rows by prefetch
+ * depths 2..4) over `nsteps` steps n = t0..t0+nsteps-1 with CUDA events on the
+ * operator's stream and keep the fastest; writes the choice and its time per
+ * step (ms) when the pointers are given.  The runs advance the operator's
+ * fields and traces: tune before setting the initial state.  Synchronises the
+ * stream.  Errors: FD_ERR_UNSUPPORTED (no tiled kernel), as
+ * fd_operator_apply otherwise. */
+fd_status fd_operator_autotune(fd_operator *op, int64_t t0, int64_t nsteps, double dt, int *best_rows,
+                               int *best_stages, double *best_ms_per_step);
+
 /* Stencil-kernel timing.  fd_operator_profile(op, n) brackets each of the
  * next n launches of the operator's grid-update kernel (the kernel that does
  * the FD update of every grid point) with CUDA events on the operator's

@@ -245,3 +245,26 @@ def num_threads():
         except ValueError:
             pass
     return os.cpu_count() or 1
+
+
+def acoustic_gradient(shape, spacing, origin, space_order, m64, eta64, dt, nt, src_coords, src_trace,
+                      rec_coords, d_obs, with_grad=True):
+    """(J, dJ/dm) of J(m) = 1/2 sum (R u - d_obs)^2, FP64, m and eta in FP64."""
+    ndim, shp, spc, org = _grid_args(shape, spacing, origin)
+    shape = tuple(int(s) for s in shape)
+    m = np.ascontiguousarray(m64, dtype=np.float64).reshape(shape)
+    eta = None if eta64 is None else np.ascontiguousarray(eta64, dtype=np.float64).reshape(shape)
+    nsrc, sc = _coords(src_coords, ndim)
+    nrec, rc_ = _coords(rec_coords, ndim)
+    st = np.ascontiguousarray(src_trace, dtype=np.float64).reshape(nt, nsrc)
+    do = np.ascontiguousarray(d_obs, dtype=np.float64).reshape(nt, nrec)
+    J = ctypes.c_double(0.0)
+    g = np.zeros(shape, dtype=np.float64) if with_grad else None
+    rcode = _lib().or_acoustic_gradient_f64(
+        ctypes.c_int(ndim), _p(shp, ctypes.c_int64), _p(spc, ctypes.c_double), _p(org, ctypes.c_double),
+        ctypes.c_int(space_order), _p(m, ctypes.c_double), _p(eta, ctypes.c_double), ctypes.c_double(dt),
+        ctypes.c_int64(nt), ctypes.c_int(nsrc), _p(sc, ctypes.c_double), _p(st, ctypes.c_double),
+        ctypes.c_int(nrec), _p(rc_, ctypes.c_double), _p(do, ctypes.c_double), ctypes.byref(J),
+        _p(g, ctypes.c_double))
+    _check(rcode, "acoustic_gradient")
+    return J.value, g

@@ -30,6 +30,9 @@
  *                           difference with `u.laplace`)
  *   or_step_points_f64      one forward update at listed points, from FP32
  *                           states, for sampled checks on large grids
+ *   or_acoustic_gradient_f64  objective 1/2 |R u - d|^2 and its adjoint-state
+ *                           gradient with respect to m (the adjoint of the
+ *                           Seismic Inversion Example used for inversion)
  */
 #include <math.h>
 #include <stdint.h>
@@ -277,4 +280,95 @@ int or_interpolate_from_f32(int ndim, const int64_t *shape, const double *spacin
     }
     or_table_free_(&tab);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint-state gradient (FP64)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Objective and gradient of J(m) = 1/2 sum_n sum_r (rec[n][r] - d[n][r])^2
+ * for the forward operator of or_acoustic_forward started from rest, with
+ * m and eta given in FP64 and eta held fixed.
+ *
+ * The forward step is u^{n+1} = 2u^n - u^{n-1} + r^n / m with
+ * r^n = dt^2 (L u^n + Q^T src[n]) - dt eta (u^n - u^{n-1}), so a change dm
+ * adds -(dm/m) (u^{n+1} - 2u^n + u^{n-1}) to u^{n+1}.  Carrying that source
+ * through the transpose of the recurrence (lambda, with mu = C lambda the
+ * adjoint state or_acoustic_adjoint computes when the residual is injected at
+ * the receivers) gives
+ *   dJ/dm(x) = -(1/dt^2) sum_{n=1}^{nt-1} mu^n(x) (u^n - 2u^{n-1} + u^{n-2})(x).
+ * This routine stores the whole forward history (small grids only), runs the
+ * adjoint recurrence backward and sums that imaging condition.
+ * grad may be NULL (objective only). */
+int or_acoustic_gradient_f64(int ndim, const int64_t *shape, const double *spacing, const double *origin,
+                             int space_order, const double *m, const double *eta, double dt, int64_t nt,
+                             int nsrc, const double *src_coords, const double *src_trace,
+                             int nrec, const double *rec_coords, const double *d_obs,
+                             double *J_out, double *grad)
+{
+    int64_t N[3];
+    if (or_dims_(ndim, shape, N) != 0 || nt < 1) return -1;
+    double coef[3][17];
+    if (stencil_coef__f64(ndim, spacing, space_order, coef) != 0) return -1;
+    int M = space_order / 2;
+    int64_t n = N[0] * N[1] * N[2];
+    double *c = (double *)malloc(sizeof(double) * n);
+    double *d = (double *)malloc(sizeof(double) * n);
+    double *hist = (double *)calloc((size_t)(nt + 2) * n, sizeof(double)); /* u^{-1} .. u^{nt} */
+    double *Lu = (double *)malloc(sizeof(double) * n);
+    double *rec = (double *)calloc((size_t)nt * (nrec > 0 ? nrec : 1), sizeof(double));
+    double *res = (double *)calloc((size_t)nt * (nrec > 0 ? nrec : 1), sizeof(double));
+    double *mu0 = (double *)calloc(n, sizeof(double));
+    double *mu1 = (double *)calloc(n, sizeof(double));
+    double *mu2 = (double *)calloc(n, sizeof(double));
+    OrTable src = {0, NULL, NULL}, rct = {0, NULL, NULL};
+    int rc = (c && d && hist && Lu && rec && res && mu0 && mu1 && mu2) ? 0 : -2;
+    if (rc == 0) rc = or_table_build_(ndim, shape, spacing, origin, nsrc, src_coords, &src);
+    if (rc == 0) rc = or_table_build_(ndim, shape, spacing, origin, nrec, rec_coords, &rct);
+    if (rc != 0) goto done;
+    for (int64_t i = 0; i < n; i++) {
+        c[i] = dt * dt / m[i];
+        d[i] = eta ? dt * eta[i] / m[i] : 0.0;
+    }
+#define U(k) (hist + (size_t)((k) + 1) * n)
+    /* forward, keeping every state; u^{-1} = u^0 = 0 */
+    for (int64_t s = 0; s < nt; s++) {
+        double *u = U(s), *up = U(s - 1), *un = U(s + 1);
+        if (nrec > 0) interpolate__f64(ndim, N, &rct, u, rec + s * nrec);
+        laplacian__f64(ndim, N, M, coef, u, Lu);
+        for (int64_t i = 0; i < n; i++) un[i] = 2 * u[i] - up[i] + c[i] * Lu[i] - d[i] * (u[i] - up[i]);
+        if (nsrc > 0) inject__f64(ndim, N, &src, c, src_trace + s * nsrc, un);
+    }
+    {
+        double J = 0.0;
+        for (int64_t k = 0; k < nt * nrec; k++) {
+            res[k] = rec[k] - d_obs[k];
+            J += 0.5 * res[k] * res[k];
+        }
+        *J_out = J;
+    }
+    if (grad) {
+        for (int64_t i = 0; i < n; i++) grad[i] = 0.0;
+        /* adjoint: mu^n = 2mu^{n+1} - mu^{n+2} + c L mu^{n+1} - d (mu^{n+1} - mu^{n+2}) + c R^T res[n] */
+        for (int64_t s = nt - 1; s >= 0; s--) {
+            laplacian__f64(ndim, N, M, coef, mu1, Lu);
+            for (int64_t i = 0; i < n; i++)
+                mu0[i] = 2 * mu1[i] - mu2[i] + c[i] * Lu[i] - d[i] * (mu1[i] - mu2[i]);
+            if (nrec > 0) inject__f64(ndim, N, &rct, c, res + s * nrec, mu0);
+            if (s >= 1) {
+                const double *a = U(s), *b = U(s - 1), *e = U(s - 2);
+                for (int64_t i = 0; i < n; i++) grad[i] -= mu0[i] * (a[i] - 2 * b[i] + e[i]) / (dt * dt);
+            }
+            double *t = mu2;
+            mu2 = mu1;
+            mu1 = mu0;
+            mu0 = t;
+        }
+    }
+#undef U
+done:
+    or_table_free_(&src);
+    or_table_free_(&rct);
+    free(c); free(d); free(hist); free(Lu); free(rec); free(res); free(mu0); free(mu1); free(mu2);
+    return rc;
 }

@@ -31,6 +31,8 @@ struct fd_sparse {
     int64_t stride;
     cudaStream_t alloc_stream;
     fdgb::SparseDev dev;
+    std::vector<int64_t> h_base;   // host copy of the table (for the fused kernel's layout)
+    std::vector<float> h_weight;
 };
 
 struct fd_operator {
@@ -328,6 +330,8 @@ extern "C" fd_status fd_sparse_create(const fd_grid *g, int npoint, const double
                                                   : cuda_error(e, "fd_sparse_create");
         }
     }
+    sp->h_base = std::move(base);
+    sp->h_weight = std::move(weight);
     SparseDev &d = sp->dev;
     d.npoint = npoint;
     d.ncorner = 1 << ndim;
@@ -410,6 +414,20 @@ static fd_status reduce_m_min(fd_operator *op)
     return FD_OK;
 }
 
+static fd_status rebuild_fused(fd_operator *op)
+{
+    if (!op->tma.ready) return FD_OK;
+    SparseHostView sv;
+    const SparseHostView *sp = nullptr;
+    if (op->src && op->src->npoint > 0) {
+        sv.npoint = op->src->npoint;
+        sv.base = op->src->h_base.data();
+        sv.weight = op->src->h_weight.data();
+        sp = &sv;
+    }
+    return tma_sparse_build(op->tma, sp, op->stream);
+}
+
 static void profile_clear(fd_operator *op)
 {
     for (cudaEvent_t e : op->prof_ev) cudaEventDestroy(e);
@@ -435,7 +453,7 @@ static void release(fd_operator *op)
     if (op->c) cudaFreeAsync(op->c, op->stream);
     if (op->d) cudaFreeAsync(op->d, op->stream);
     if (op->status) cudaFreeAsync(op->status, op->stream);
-    tma_plan_release(op->tma);
+    tma_plan_release(op->tma, op->stream);
     delete op;
 }
 
@@ -502,6 +520,8 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     }
     s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
     if (s != FD_OK) { release(op); return s; }
+    s = rebuild_fused(op);
+    if (s != FD_OK) { release(op); return s; }
     op->cluster_ok = op->kind == FD_DIFFUSION_EULER &&
                      diffusion_cluster_fits(op->so / 2, op->geom, &op->cluster_n, &op->cluster_smem);
     *out = op;
@@ -542,7 +562,7 @@ extern "C" fd_status fd_operator_bind(fd_operator *op, const char *name, void *o
         if (op->kind != FD_ACOUSTIC_LEAPFROG && sp)
             return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: sparse points only for the acoustic operator");
         (n == "src" ? op->src : op->rec) = sp;
-        return FD_OK;
+        return rebuild_fused(op);
     }
     if (n == "stream") {
         op->stream = (cudaStream_t)obj;
@@ -557,60 +577,95 @@ extern "C" fd_status fd_operator_bind(fd_operator *op, const char *name, void *o
     return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: unknown name '%s'", name);
 }
 
+// Stability check of fd_operator_apply / fd_operator_step.
+static fd_status check_dt(const fd_operator *op, double dt, const char *who)
+{
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(FD_ERR_INVALID_ARG, "%s: dt must be > 0", who);
+    if (op->flags & FD_FLAG_NO_CFL_CHECK) return FD_OK;
+    if (op->kind == FD_ACOUSTIC_LEAPFROG) {
+        double limit = 2.0 * std::sqrt(op->m_min / op->lambda_max);
+        if (dt > limit) return set_error(FD_ERR_UNSTABLE, "%s: dt = %g above the stability limit %g", who, dt, limit);
+    } else {
+        double limit = 2.0 / (op->a * op->lambda_max);
+        if (dt > limit)
+            return set_error(FD_ERR_UNSTABLE, "%s: a*dt = %g above the Euler limit %g", who, op->a * dt, op->a * limit);
+    }
+    return FD_OK;
+}
+
+// Recompute c, d (and the damping flags of the tiled kernel) when dt or the
+// inputs changed.
+static fd_status prepare_coefficients(fd_operator *op, double dt)
+{
+    if (op->kind != FD_ACOUSTIC_LEAPFROG || op->coef_dt == dt) return FD_OK;
+    cudaStream_t st = op->stream;
+    FD_CUDA(launch_coefficients(op->geom, op->m->slot[0], op->eta ? op->eta->slot[0] : nullptr, dt, op->c, op->d, st),
+            "coefficients");
+    op->launches += 1;
+    if (op->tma.ready) {
+        FD_CUDA(launch_damping_flags(op->tma, st), "damping flags");
+        op->launches += 1;
+    }
+    op->coef_dt = dt;
+    return FD_OK;
+}
+
 extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt)
 {
     if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: null operator");
     if (nt < 0 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: need t0 >= 0, nt >= 0");
-    if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: dt must be > 0");
     const bool reverse = (op->flags & FD_FLAG_REVERSE) != 0;
     for (fd_sparse *sp : {op->src, op->rec})
         if (sp && sp->npoint > 0 && t0 + nt > sp->nt)
             return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: trace has %lld rows, need %lld",
                              (long long)sp->nt, (long long)(t0 + nt));
-    if (!(op->flags & FD_FLAG_NO_CFL_CHECK)) {
-        if (op->kind == FD_ACOUSTIC_LEAPFROG) {
-            double limit = 2.0 * std::sqrt(op->m_min / op->lambda_max);
-            if (dt > limit)
-                return set_error(FD_ERR_UNSTABLE, "fd_operator_apply: dt = %g above the stability limit %g", dt, limit);
-        } else {
-            double limit = 2.0 / (op->a * op->lambda_max);
-            if (dt > limit)
-                return set_error(FD_ERR_UNSTABLE, "fd_operator_apply: a*dt = %g above the Euler limit %g", op->a * dt,
-                                 op->a * limit);
-        }
-    }
+    fd_status cs = check_dt(op, dt, "fd_operator_apply");
+    if (cs != FD_OK) return cs;
     if (nt == 0) return FD_OK;
     const int M = op->so / 2;
     const Geom &g = op->geom;
     cudaStream_t st = op->stream;
     const bool plain = (op->flags & FD_FLAG_PLAIN_KERNELS) != 0 || !op->tma.ready;
     if (op->kind == FD_ACOUSTIC_LEAPFROG) {
-        if (op->coef_dt != dt) {
-            FD_CUDA(launch_coefficients(g, op->m->slot[0], op->eta ? op->eta->slot[0] : nullptr, dt, op->c, op->d, st),
-                    "coefficients");
-            op->launches += 1;
-            op->coef_dt = dt;
-        }
+        cs = prepare_coefficients(op, dt);
+        if (cs != FD_OK) return cs;
         for (int64_t q = 0; q < nt; q++) {
             int64_t n = reverse ? t0 + nt - 1 - q : t0 + q;
             int cur = (int)((reverse ? n + 1 : n) & 1);
             float *u = op->u->slot[cur];
             float *up = op->u->slot[cur ^ 1];
-            if (op->rec && op->rec->npoint > 0) {
-                FD_CUDA(launch_interpolate(op->rec->dev, u, op->rec->trace + n * op->rec->stride, st), "interpolate");
-                op->launches += 1;
-            }
-            FD_CUDA(profile_mark(op, 0), "profile");
+            float *rec_row = (op->rec && op->rec->npoint > 0) ? op->rec->trace + n * op->rec->stride : nullptr;
+            const float *src_row =
+                (op->src && op->src->npoint > 0) ? op->src->trace + n * op->src->stride : nullptr;
             if (plain) {
-                FD_CUDA(launch_acoustic_plain(M, g, op->coef, u, up, op->c, op->d, st), "acoustic step");
-            } else {
-                FD_CUDA(launch_acoustic_tma(op->tma, M, g, op->coef, cur, op->status, st), "acoustic step");
-            }
-            FD_CUDA(profile_mark(op, 1), "profile");
-            op->launches += 1;
-            if (op->src && op->src->npoint > 0) {
-                FD_CUDA(launch_inject(op->src->dev, op->c, op->src->trace + n * op->src->stride, up, st), "inject");
+                if (rec_row) {
+                    FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
+                    op->launches += 1;
+                }
+                FD_CUDA(profile_mark(op, 0), "profile");
+                FD_CUDA(launch_acoustic_plain(M, g, op->coef, u, up, up, op->c, op->d, st), "acoustic step");
+                FD_CUDA(profile_mark(op, 1), "profile");
                 op->launches += 1;
+                if (src_row) {
+                    FD_CUDA(launch_inject(op->src->dev, op->c, src_row, up, st), "inject");
+                    op->launches += 1;
+                }
+            } else {
+                // receivers: a small kernel reading u^n; sources: fused into
+                // the tiled kernel when the per-tile lists fit in shared memory
+                if (rec_row) {
+                    FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
+                    op->launches += 1;
+                }
+                FD_CUDA(profile_mark(op, 0), "profile");
+                FD_CUDA(launch_acoustic_tma(op->tma, M, g, op->coef, cur, op->status, src_row, st),
+                        "acoustic step");
+                FD_CUDA(profile_mark(op, 1), "profile");
+                op->launches += 1;
+                if (src_row && !op->tma.has_src) {
+                    FD_CUDA(launch_inject(op->src->dev, op->c, src_row, up, st), "inject");
+                    op->launches += 1;
+                }
             }
         }
     } else if (op->cluster_ok && !(op->flags & FD_FLAG_PLAIN_KERNELS)) {
@@ -701,5 +756,171 @@ extern "C" fd_status fd_operator_profile_read(fd_operator *op, double *total_ms,
     }
     *total_ms = sum;
     *launches = op->prof_used;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_step(fd_operator *op, int64_t n, double dt, const void *u_cur, const void *u_prev,
+                                      void *u_next)
+{
+    if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_step: null operator");
+    if (op->kind != FD_ACOUSTIC_LEAPFROG)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_step: acoustic operators only");
+    if (!u_cur || !u_prev || !u_next) return set_error(FD_ERR_INVALID_ARG, "fd_operator_step: null buffer");
+    if (u_next == u_cur) return set_error(FD_ERR_INVALID_ARG, "fd_operator_step: u_next must differ from u_cur");
+    for (const void *p : {u_cur, u_prev, (const void *)u_next})
+        if (((uintptr_t)p) % 32 != 0) return set_error(FD_ERR_LAYOUT, "fd_operator_step: buffer not 32-byte aligned");
+    if (n < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_step: n < 0");
+    for (fd_sparse *sp : {op->src, op->rec})
+        if (sp && sp->npoint > 0 && n >= sp->nt)
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_step: trace has %lld rows, need row %lld",
+                             (long long)sp->nt, (long long)n);
+    fd_status cs = check_dt(op, dt, "fd_operator_step");
+    if (cs != FD_OK) return cs;
+    cs = prepare_coefficients(op, dt);
+    if (cs != FD_OK) return cs;
+    const int M = op->so / 2;
+    cudaStream_t st = op->stream;
+    const float *uc = (const float *)u_cur;
+    const float *up = (const float *)u_prev;
+    float *un = (float *)u_next;
+    float *rec_row = (op->rec && op->rec->npoint > 0) ? op->rec->trace + n * op->rec->stride : nullptr;
+    const float *src_row = (op->src && op->src->npoint > 0) ? op->src->trace + n * op->src->stride : nullptr;
+    const bool plain = (op->flags & FD_FLAG_PLAIN_KERNELS) != 0 || !op->tma.ready;
+    if (plain) {
+        if (rec_row) {
+            FD_CUDA(launch_interpolate(op->rec->dev, uc, rec_row, st), "interpolate");
+            op->launches += 1;
+        }
+        FD_CUDA(profile_mark(op, 0), "profile");
+        FD_CUDA(launch_acoustic_plain(M, op->geom, op->coef, uc, up, un, op->c, op->d, st), "acoustic step");
+        FD_CUDA(profile_mark(op, 1), "profile");
+        op->launches += 1;
+        if (src_row) {
+            FD_CUDA(launch_inject(op->src->dev, op->c, src_row, un, st), "inject");
+            op->launches += 1;
+        }
+    } else {
+        if (rec_row) {
+            FD_CUDA(launch_interpolate(op->rec->dev, uc, rec_row, st), "interpolate");
+            op->launches += 1;
+        }
+        FD_CUDA(profile_mark(op, 0), "profile");
+        FD_CUDA(launch_acoustic_tma_buffers(op->tma, M, op->coef, uc, up, un, op->status, src_row, st),
+                "acoustic step");
+        FD_CUDA(profile_mark(op, 1), "profile");
+        op->launches += 1;
+        if (src_row && !op->tma.has_src) {
+            FD_CUDA(launch_inject(op->src->dev, op->c, src_row, un, st), "inject");
+            op->launches += 1;
+        }
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_imaging_accumulate(const fd_grid *g, double scale, const void *mu, const void *u0,
+                                           const void *u1, const void *u2, void *grad, void *cuda_stream)
+{
+    if (!g || !mu || !u0 || !u1 || !u2 || !grad)
+        return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate: null pointer");
+    for (const void *p : {mu, u0, u1, u2, (const void *)grad})
+        if (((uintptr_t)p) % 16 != 0) return set_error(FD_ERR_LAYOUT, "fd_imaging_accumulate: buffer not aligned");
+    FD_CUDA(launch_imaging(geom_of(*g), (float)scale, (const float *)mu, (const float *)u0, (const float *)u1,
+                           (const float *)u2, (float *)grad, (cudaStream_t)cuda_stream),
+            "fd_imaging_accumulate");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stages)
+{
+    if (!op || rows < 0 || stages < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_set_tiling: bad arguments");
+    if (!op->tma.ready && (rows > 0 || stages > 0))
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_set_tiling: this operator has no tiled kernel");
+    FD_CUDA(cudaStreamSynchronize(op->stream), "fd_operator_set_tiling");
+    const int old_rows = op->tma.force_rows, old_stages = op->tma.force_stages;
+    op->tma.force_rows = rows;
+    op->tma.force_stages = stages;
+    op->tma.cache.clear();
+    // the damping flags are laid out per tile: rebuild them for the new tiling
+    if (op->tma.dflags) {
+        cudaFree(op->tma.dflags);
+        op->tma.dflags = nullptr;
+        op->tma.nz_count = nullptr;
+    }
+    fd_status s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+    if (s != FD_OK) {
+        op->tma.force_rows = old_rows;
+        op->tma.force_stages = old_stages;
+        tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+        rebuild_fused(op);
+        op->coef_dt = -1.0;
+        return s;
+    }
+    s = rebuild_fused(op);
+    op->coef_dt = -1.0;  // recompute the coefficients and the damping flags
+    return s;
+}
+
+extern "C" fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, int *stages, int *ctas)
+{
+    if (!op || !rows || !stages || !ctas) return set_error(FD_ERR_INVALID_ARG, "fd_operator_get_tiling: null pointer");
+    tma_plan_tiling(op->tma, rows, stages, ctas);
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_autotune(fd_operator *op, int64_t t0, int64_t nsteps, double dt, int *best_rows,
+                                          int *best_stages, double *best_ms_per_step)
+{
+    if (!op || nsteps < 1 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_autotune: bad arguments");
+    if (!op->tma.ready) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_autotune: no tiled kernel to tune");
+    static const int kRows[] = {8, 10, 12, 14, 16, 18, 20, 24, 27, 32};
+    cudaEvent_t e0, e1;
+    FD_CUDA(cudaEventCreate(&e0), "fd_operator_autotune");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(FD_ERR_CUDA, "fd_operator_autotune: cudaEventCreate");
+    }
+    int br = 0, bs = 0;
+    double bms = 1e30;
+    fd_status last = FD_OK;
+    for (int rows : kRows) {
+        for (int stages = 2; stages <= 4; stages++) {
+            // several heights can round to the same balanced strips: time once
+            bool seen = false;
+            for (int prev : kRows) {
+                if (prev >= rows) break;
+                if ((op->geom.n[1] + prev - 1) / prev == (op->geom.n[1] + rows - 1) / rows) seen = true;
+            }
+            if (seen) continue;
+            if (fd_operator_set_tiling(op, rows, stages) != FD_OK) continue;
+            last = fd_operator_apply(op, t0, nsteps < 3 ? nsteps : 3, dt);  // warm-up, coefficients
+            if (last != FD_OK) break;
+            cudaEventRecord(e0, op->stream);
+            last = fd_operator_apply(op, t0, nsteps, dt);
+            cudaEventRecord(e1, op->stream);
+            if (last != FD_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                last = set_error(FD_ERR_CUDA, "fd_operator_autotune: timing");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / (double)nsteps;
+            if (per < bms) {
+                bms = per;
+                br = rows;
+                bs = stages;
+            }
+        }
+        if (last != FD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (last != FD_OK) return last;
+    if (br == 0) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_autotune: no tiling fits");
+    fd_status s = fd_operator_set_tiling(op, br, bs);
+    if (s != FD_OK) return s;
+    if (best_rows) *best_rows = br;
+    if (best_stages) *best_stages = bs;
+    if (best_ms_per_step) *best_ms_per_step = bms;
     return FD_OK;
 }

@@ -47,9 +47,13 @@ cudaError_t launch_inject(const SparseDev &sp, const float *c, const float *row,
                           cudaStream_t st);
 
 // plain kernels: one thread per (d1, d2) column, streaming d0
+// reads u (u^n) and up (u^{n-1}), writes out (u^{n+1}); out may equal up
 cudaError_t launch_acoustic_plain(int half_width, const Geom &g, const Coef &cf,
-                                  const float *u, float *u_prev_out, const float *c,
+                                  const float *u, const float *up, float *out, const float *c,
                                   const float *d, cudaStream_t st);
+// grad += scale * mu * (u0 - 2 u1 + u2)
+cudaError_t launch_imaging(const Geom &g, float scale, const float *mu, const float *u0,
+                           const float *u1, const float *u2, float *grad, cudaStream_t st);
 cudaError_t launch_diffusion_plain(int half_width, const Geom &g, const Coef &cf, float adt,
                                    const float *u, float *u_out, cudaStream_t st);
 

@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "fd_internal.h"
 
 namespace fdgb {
@@ -22,29 +24,91 @@ struct TileArgs {
     int box_h;           // rows of a haloed tile: rows_max + 2M
 };
 
+// One injected corner: its d0 plane, row and column inside the owning tile,
+// the source's trace column and the linear weight.
+struct SrcEntry {
+    int z;
+    int r;
+    int x;
+    int p;
+    float w;
+};
+
+// Device table of the fused source injection, sorted by (tile, plane), with
+// per-tile ranges.
+struct SparseFused {
+    const SrcEntry *src = nullptr;
+    const int *src_off = nullptr;   // [tiles + 1]
+};
+
+// Host view of a sparse object's interpolation table.
+struct SparseHostView {
+    int npoint;
+    const int64_t *base;
+    const float *weight;  // [npoint][8]
+};
+
 struct TmaPlan {
     bool ready = false;
+    int force_rows = 0;    // > 0: tile height chosen by the caller (autotuner)
+    int force_stages = 0;  // > 0: prefetch depth chosen by the caller
     int kind = 0;
     int M = 0;
     int stages = 0;      // prefetch depth P
     TileArgs args{};
     int threads = 0;
-    size_t smem = 0;
+    size_t smem = 0;       // dynamic shared memory of a launch
+    size_t smem_max = 0;   // the device's opt-in limit
     CUtensorMap u_halo[2];   // slot s of u, haloed box (kBoxW x box_h x 1)
     CUtensorMap u_tile[2];   // slot s of u, tile box (kTileW x rows_max x 1)
     CUtensorMap c_tile, d_tile;
     float *slot[2] = {nullptr, nullptr};
+    const float *d = nullptr;
+    // per (tile, d0 plane): 1 if d = dt*eta/m is non-zero somewhere on it, so
+    // the kernel skips the d box of all-zero blocks (outside the sponge)
+    unsigned char *dflags = nullptr;
+    unsigned long long *nz_count = nullptr;  // grid points with d != 0
+    // fused receiver interpolation / source injection (library-owned)
+    SparseFused fused;
+    void *fused_mem = nullptr;
+    bool has_src = false;
+    int src_cap = 0;  // injected corners per tile staged in shared memory
+    // tensor maps of buffers other than the two slots (out-of-place steps)
+    struct CachedMap {
+        const void *ptr;
+        bool halo;
+        CUtensorMap map;
+    };
+    std::vector<CachedMap> cache;
 };
 
 // Build the plan for an operator (3D acoustic only; other cases leave
 // plan.ready false and use the plain kernels).
 fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g,
                          float *const slot[2], float *c, float *d);
-void tma_plan_release(TmaPlan &plan);
+void tma_plan_release(TmaPlan &plan, cudaStream_t st);
+
+// Tile height and prefetch depth of a built plan (for reporting).
+void tma_plan_tiling(const TmaPlan &plan, int *rows, int *stages, int *ctas);
+
+// Recompute plan.dflags (and the non-zero count) from the d field; enqueue on st.
+cudaError_t launch_damping_flags(const TmaPlan &plan, cudaStream_t st);
+
+// One acoustic step between arbitrary buffers: reads u_cur (haloed) and
+// u_prev, writes u_next (may equal u_prev).  Tensor maps are encoded on first
+// use of a buffer and cached.
+cudaError_t launch_acoustic_tma_buffers(TmaPlan &plan, int M, const Coef &cf, const float *u_cur,
+                                        const float *u_prev, float *u_next, int *status,
+                                        const float *src_row, cudaStream_t st);
+
+// Build the fused source-injection table of the plan (src may be null or
+// empty); leaves has_src false when the per-tile lists do not fit.
+fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_t st);
 
 // One acoustic step: reads slot `cur` (u^n) and slot cur^1 (u^{n-1}),
-// overwrites slot cur^1 with u^{n+1}.
+// overwrites slot cur^1 with u^{n+1}; adds c Q^T src_row when src_row is
+// given and the plan fuses the sources.
 cudaError_t launch_acoustic_tma(const TmaPlan &plan, int M, const Geom &g, const Coef &cf,
-                                int cur, int *status, cudaStream_t st);
+                                int cur, int *status, const float *src_row, cudaStream_t st);
 
 }  // namespace fdgb

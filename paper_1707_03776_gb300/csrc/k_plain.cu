@@ -113,7 +113,7 @@ __device__ __forceinline__ float laplacian_at(const Geom &g, const Coef &cf,
 //   u_prev <- 2u - u_prev + c L u - d (u - u_prev)
 template <int M, bool THREE_D>
 __global__ void acoustic_plain_kernel(Geom g, Coef cf, const float *__restrict__ u,
-                                      float *__restrict__ up, const float *__restrict__ c,
+                                      const float *up, float *out, const float *__restrict__ c,
                                       const float *__restrict__ d)
 {
     int64_t i2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -124,7 +124,40 @@ __global__ void acoustic_plain_kernel(Geom g, Coef cf, const float *__restrict__
         float lap = laplacian_at<M, THREE_D>(g, cf, u, at, i0, i1, i2);
         float uc = u[at];
         float upv = up[at];
-        up[at] = 2.0f * uc - upv + c[at] * lap - d[at] * (uc - upv);
+        out[at] = 2.0f * uc - upv + c[at] * lap - d[at] * (uc - upv);
+    }
+}
+
+// grad += scale * mu * (u0 - 2 u1 + u2) over the interior: the imaging
+// condition of the adjoint-state gradient with respect to m.
+__global__ void imaging_kernel(Geom g, float scale, const float *__restrict__ mu,
+                               const float *__restrict__ u0, const float *__restrict__ u1,
+                               const float *__restrict__ u2, float *__restrict__ grad)
+{
+    const int64_t rows = g.n[0] * g.n[1];
+    const int64_t groups = (g.n[2] + 3) / 4;  // float4 groups per row
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows * groups;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = q / groups;
+        const int64_t c0 = 4 * (q - row * groups);
+        const int64_t i0 = row / g.n[1];
+        const int64_t i1 = row - i0 * g.n[1];
+        const int64_t at = i0 * g.s0 + i1 * g.s1 + c0;
+        if (c0 + 4 <= g.n[2]) {
+            const float4 m4 = *reinterpret_cast<const float4 *>(mu + at);
+            const float4 a = *reinterpret_cast<const float4 *>(u0 + at);
+            const float4 b = *reinterpret_cast<const float4 *>(u1 + at);
+            const float4 e = *reinterpret_cast<const float4 *>(u2 + at);
+            float4 gr = *reinterpret_cast<const float4 *>(grad + at);
+            gr.x = fmaf(scale * m4.x, a.x - 2.0f * b.x + e.x, gr.x);
+            gr.y = fmaf(scale * m4.y, a.y - 2.0f * b.y + e.y, gr.y);
+            gr.z = fmaf(scale * m4.z, a.z - 2.0f * b.z + e.z, gr.z);
+            gr.w = fmaf(scale * m4.w, a.w - 2.0f * b.w + e.w, gr.w);
+            *reinterpret_cast<float4 *>(grad + at) = gr;
+        } else {
+            for (int64_t k = 0; c0 + k < g.n[2]; k++)
+                grad[at + k] = fmaf(scale * mu[at + k], u0[at + k] - 2.0f * u1[at + k] + u2[at + k], grad[at + k]);
+        }
     }
 }
 
@@ -188,8 +221,16 @@ cudaError_t launch_inject(const SparseDev &sp, const float *c, const float *row,
 
 #define FD_FOR_EACH_M(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
 
+cudaError_t launch_imaging(const Geom &g, float scale, const float *mu, const float *u0, const float *u1,
+                           const float *u2, float *grad, cudaStream_t st)
+{
+    int64_t total = g.n[0] * g.n[1] * ((g.n[2] + 3) / 4);
+    imaging_kernel<<<grid_stride_blocks(total), kThreads, 0, st>>>(g, scale, mu, u0, u1, u2, grad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_acoustic_plain(int M, const Geom &g, const Coef &cf, const float *u,
-                                  float *up, const float *c, const float *d, cudaStream_t st)
+                                  const float *up, float *out, const float *c, const float *d, cudaStream_t st)
 {
     dim3 grid((unsigned)((g.n[2] + 127) / 128), (unsigned)g.n[1]);
     bool three = g.ndim == 3;
@@ -197,9 +238,9 @@ cudaError_t launch_acoustic_plain(int M, const Geom &g, const Coef &cf, const fl
 #define CASE(MM)                                                                          \
     case MM:                                                                              \
         if (three)                                                                        \
-            acoustic_plain_kernel<MM, true><<<grid, 128, 0, st>>>(g, cf, u, up, c, d);    \
-        else                                                                              \
-            acoustic_plain_kernel<MM, false><<<grid, 128, 0, st>>>(g, cf, u, up, c, d);   \
+            acoustic_plain_kernel<MM, true><<<grid, 128, 0, st>>>(g, cf, u, up, out, c, d);  \
+        else                                                                                \
+            acoustic_plain_kernel<MM, false><<<grid, 128, 0, st>>>(g, cf, u, up, out, c, d); \
         break;
         FD_FOR_EACH_M(CASE)
 #undef CASE

@@ -75,6 +75,13 @@ _SIGNATURES = [
     ("fd_operator_profile", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("fd_operator_profile_read", ctypes.c_int, [_vp, _c_f64p, _c_i64p]),
     ("fd_interpolate_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _c_f64p, _vp, _vp, _vp]),
+    ("fd_operator_step", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp]),
+    ("fd_imaging_accumulate", ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fd_operator_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    ("fd_operator_autotune", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _c_f64p]),
+    ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
 ]
 
 FD_NOALLOC_MAX_POINTS = 65536
@@ -242,6 +249,35 @@ def fd_operator_profile_read(op):
     n = ctypes.c_int64(0)
     _check(lib().fd_operator_profile_read(op, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def fd_operator_step(op, n, dt, u_cur, u_prev, u_next):
+    """One out-of-place step between device buffers (data pointers)."""
+    _check(lib().fd_operator_step(op, int(n), float(dt), int(u_cur), int(u_prev), int(u_next)))
+
+
+def fd_imaging_accumulate(grid, scale, mu, u0, u1, u2, grad, stream=0):
+    """grad += scale * mu * (u0 - 2 u1 + u2) (device pointers)."""
+    _check(lib().fd_imaging_accumulate(grid, float(scale), int(mu), int(u0), int(u1), int(u2), int(grad),
+                                       int(stream) or None))
+
+
+def fd_operator_set_tiling(op, rows=0, stages=0):
+    _check(lib().fd_operator_set_tiling(op, int(rows), int(stages)))
+
+
+def fd_operator_autotune(op, t0, nsteps, dt):
+    """Time candidate tilings and keep the fastest: (rows, stages, ms per step)."""
+    r, st, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib().fd_operator_autotune(op, int(t0), int(nsteps), float(dt), ctypes.byref(r), ctypes.byref(st),
+                                      ctypes.byref(ms)))
+    return r.value, st.value, ms.value
+
+
+def fd_operator_get_tiling(op):
+    r, s, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().fd_operator_get_tiling(op, ctypes.byref(r), ctypes.byref(s), ctypes.byref(c)))
+    return r.value, s.value, c.value
 
 
 def fd_interpolate_noalloc(grid, coords, dev_field, dev_out, stream=0):

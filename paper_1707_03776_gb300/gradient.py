@@ -1,0 +1,170 @@
+"""Adjoint-state gradient of the acoustic forward operator with respect to m,
+with checkpointing, behind a torch.autograd.Function.
+
+Forward: the operator of the Seismic Inversion Example run from rest; every
+`checkpoint_every` steps the two wavefield levels are copied aside.
+Backward: the paper's adjoint operator (the same update run backward in time
+with the receiver residual injected, FD_FLAG_REVERSE) sweeps the checkpoint
+segments from last to first; inside each segment the forward states are
+recomputed from its checkpoint with out-of-place steps (fd_operator_step) into
+a segment buffer, and the imaging condition
+    dJ/dm += -(1/dt^2) mu^n (u^n - 2u^{n-1} + u^{n-2})
+is accumulated by fd_imaging_accumulate after every adjoint step.
+
+Every step of the path runs in libfdgb's kernels; torch provides the device
+memory (fields, checkpoints, the segment buffer) and the autograd plumbing.
+"""
+import numpy as np
+
+from . import fd
+
+
+class Shot:
+    """One seismic experiment: source positions and wavelets, receiver
+    positions, on a grid."""
+
+    def __init__(self, src_coords, src_trace, rec_coords):
+        self.src_coords = np.ascontiguousarray(src_coords, dtype=np.float64)
+        self.src_trace = np.ascontiguousarray(src_trace, dtype=np.float32)
+        self.rec_coords = np.ascontiguousarray(rec_coords, dtype=np.float64)
+
+
+class Propagator:
+    """Device-resident forward and adjoint operators for one grid and shot."""
+
+    def __init__(self, shape, spacing, origin, space_order, shot, nt, dt, checkpoint_every=50, flags=0):
+        import torch
+        self.torch = torch
+        self.shape = tuple(int(s) for s in shape)
+        self.nt = int(nt)
+        self.dt = float(dt)
+        self.k = int(checkpoint_every)
+        self.grid = fd.Grid(self.shape, spacing, origin)
+        self.m = fd.DenseData("m", self.grid)
+        self.eta = fd.DenseData("eta", self.grid)
+        self.m.data.fill_(1.0)
+        self.u = fd.TimeData("u", self.grid)
+        self.src = fd.PointData("src", self.grid, shot.src_coords, self.nt)
+        self.src.data[:, : self.src.npoint].copy_(torch.from_numpy(shot.src_trace.reshape(self.nt, -1)))
+        self.rec = fd.PointData("rec", self.grid, shot.rec_coords, self.nt)
+        # forward with receivers; recomputation without them
+        self.fwd = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, space_order, self.u, self.m, self.eta, src=self.src,
+                               rec=self.rec, flags=flags)
+        self.re = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, space_order, self.u, self.m, self.eta, src=self.src,
+                              flags=flags)
+        # adjoint: residual injected at the receiver positions, backward in time
+        self.mu = fd.TimeData("mu", self.grid)
+        self.res = fd.PointData("res", self.grid, shot.rec_coords, self.nt)
+        self.adj = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, space_order, self.mu, self.m, self.eta, src=self.res,
+                               flags=flags | fd.FD_FLAG_REVERSE)
+        nseg = (self.nt + self.k - 1) // self.k
+        ps = self.grid.padded_shape
+        # checkpoint j: the states of times jk-1 and jk-2 (zero for j = 0)
+        self.ckpt = torch.zeros((nseg, 2) + ps, dtype=torch.float32, device="cuda")
+        # segment buffer: states of times jk-2 .. (j+1)k-1
+        self.seg = torch.zeros((self.k + 2,) + ps, dtype=torch.float32, device="cuda")
+        self.grad = fd.DenseData("grad", self.grid)
+
+    def set_damping(self, eta):
+        """Damping eta (held fixed by the gradient)."""
+        torch = self.torch
+        t = eta if isinstance(eta, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(eta, dtype=np.float32))
+        self.eta.data.copy_(t.reshape(self.shape))
+        for op in (self.fwd, self.re, self.adj):
+            op.bind("eta", self.eta)
+
+    def set_model(self, m, eta=None):
+        torch = self.torch
+        self.m.data.copy_(m.reshape(self.shape))
+        if eta is not None:
+            self.eta.data.copy_(eta.reshape(self.shape))
+        for op in (self.fwd, self.re, self.adj):
+            op.bind("m", self.m)
+            op.bind("eta", self.eta)
+
+    def forward(self):
+        """Forward run from rest with checkpoints; returns the device traces."""
+        for s in self.u.slots:
+            s.zero_()
+        self.ckpt[0].zero_()
+        k = self.k
+        done = 0
+        for j in range(1, self.ckpt.shape[0]):
+            # run up to time jk-1, then keep u^{jk-1} (slot (jk-1)%2) and
+            # u^{jk-2} (the other slot)
+            t = j * k - 1
+            self.fwd.apply(done, t - done, self.dt)
+            done = t
+            self.ckpt[j, 0].copy_(self.u.slots[t % 2])
+            self.ckpt[j, 1].copy_(self.u.slots[(t + 1) % 2])
+        self.fwd.apply(done, self.nt - done, self.dt)
+        return self.rec.data[:, : self.rec.npoint]
+
+    def backward(self, residual):
+        """Adjoint run with `residual` [nt, nrec] injected; returns dJ/dm as an
+        interior view (grid shape) of the library's gradient buffer."""
+        torch = self.torch
+        self.res.data[:, : self.res.npoint].copy_(residual)
+        for s in self.mu.slots:
+            s.zero_()
+        self.grad.slots[0].zero_()
+        g = self.grid.handle
+        stream = torch.cuda.current_stream().cuda_stream
+        scale = -1.0 / (self.dt * self.dt)
+        k = self.k
+        seg = self.seg
+        for j in range(self.ckpt.shape[0] - 1, -1, -1):
+            n_lo = j * k
+            n_hi = min((j + 1) * k, self.nt)
+            # seg[i] holds the state of time n_lo - 2 + i
+            seg[1].copy_(self.ckpt[j, 0])
+            seg[0].copy_(self.ckpt[j, 1])
+            for t in range(n_lo - 1, n_hi - 1):
+                i = t - (n_lo - 2)
+                if t < 0:
+                    # u^0 from rest: only the source term of step -1 is absent
+                    seg[i + 1].zero_()
+                    continue
+                fd.fd_operator_step(self.re.handle, t, self.dt, seg[i].data_ptr(), seg[i - 1].data_ptr(),
+                                    seg[i + 1].data_ptr())
+            for n in range(n_hi - 1, n_lo - 1, -1):
+                self.adj.apply(n, 1, self.dt)
+                if n >= 1:
+                    i = n - (n_lo - 2)
+                    fd.fd_imaging_accumulate(g, scale, self.mu.slots[n % 2].data_ptr(), seg[i].data_ptr(),
+                                             seg[i - 1].data_ptr(), seg[i - 2].data_ptr(),
+                                             self.grad.slots[0].data_ptr(), stream)
+        return self.grad.data
+
+
+def _autograd_function():
+    import torch
+
+    class AcousticModelling(torch.autograd.Function):
+        """rec = F(m): forward modelling; backward = adjoint-state gradient."""
+
+        @staticmethod
+        def forward(ctx, m, prop):
+            prop.set_model(m)
+            rec = prop.forward().clone()
+            ctx.prop = prop
+            return rec
+
+        @staticmethod
+        def backward(ctx, grad_rec):
+            g = ctx.prop.backward(grad_rec.contiguous()).clone()
+            return g, None
+
+    return AcousticModelling
+
+
+_FN = None
+
+
+def modelling(m, prop):
+    """Differentiable forward modelling: receiver traces of the shot of `prop`
+    for square slowness m (a CUDA tensor of the grid's shape)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(m, prop)

@@ -49,6 +49,16 @@ class AcousticModel:
         self.op.bind("m", self.m)
         self.op.bind("eta", self.eta)
 
+    def autotune(self, dt, nsteps=20):
+        """Pick the fastest tiling on this model's data (leaves u zeroed)."""
+        for s in self.u.slots:
+            s.zero_()
+        best = fd.fd_operator_autotune(self.op.handle, 0, nsteps, dt)
+        for s in self.u.slots:
+            s.zero_()
+        self.op.sync()
+        return best
+
     def run(self, dt):
         """One forward run from rest on device-resident inputs."""
         for s in self.u.slots:

@@ -163,3 +163,40 @@ def random_smooth_velocity(shape, seed, sigma_cells=8.0, vmin=1500.0, vmax=4500.
         u = np.fft.irfft(np.fft.rfft(u, axis=a) * filt.reshape(sh), n=n, axis=a)
     u = (u - u.min()) / (u.max() - u.min())
     return vmin + (vmax - vmin) * u
+
+
+def gradient_config(n=256, nt=1500, nshots=8, nrec_side=65, h=10.0, space_order=8, sponge=40, f0=10.0):
+    """Adjoint/gradient workload: true model two-layer (1500/2500 m/s) plus a
+    Gaussian anomaly of +10 % velocity with a 30-cell radius at the centre;
+    the starting model is the true background smoothed with a wide Gaussian
+    (no anomaly); `nshots` sources on a line at the surface (depth index
+    sponge), `nrec_side`^2 receivers half a cell below them; dt at CFL 0.4 of
+    the fastest velocity."""
+    shape = (n,) * 3
+    spacing = (h,) * 3
+    v_bg = two_layer_velocity(shape, 1500.0, 2500.0)
+    idx = np.arange(n, dtype=np.float64)
+    c = (n - 1) / 2.0
+    X, Y, Z = np.meshgrid(idx, idx, idx, indexing="ij", sparse=True)
+    r2 = (X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2
+    v_true = v_bg * (1.0 + 0.10 * np.exp(-r2 / (2.0 * (30.0 / 2.0) ** 2)))
+    # smooth starting model: the background convolved with a Gaussian (sigma 10 cells)
+    v0 = v_bg.copy()
+    k = np.fft.rfftfreq(n)
+    filt = np.exp(-0.5 * (2 * math.pi * k * 10.0) ** 2)
+    v0 = np.fft.irfft(np.fft.rfft(v0, axis=2) * filt.reshape(1, 1, -1), n=n, axis=2)
+    v_max = float(max(v_true.max(), v0.max()))
+    dt = 0.4 * h / v_max
+    m_true = (1.0 / v_true ** 2).astype(np.float32)
+    m0 = (1.0 / v0 ** 2).astype(np.float32)
+    sigma = sponge_sigma(shape, spacing, sponge, v_max, ref_width=max(sponge, 40))
+    eta = (m0.astype(np.float64) * sigma).astype(np.float32)
+    depth = float(sponge)
+    xs = np.linspace(sponge + 10.0, n - 1 - sponge - 10.0, nshots)
+    shots = [np.array([[x * h, c * h, depth * h]]) for x in xs]
+    g = np.linspace(float(sponge), float(n - 1 - sponge), nrec_side)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    rec = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, depth + 0.5)], axis=1) * h
+    wavelet = ricker(nt, dt, f0).astype(np.float32).reshape(nt, 1)
+    return dict(shape=shape, spacing=spacing, origin=(0.0, 0.0, 0.0), space_order=space_order, m_true=m_true,
+                m0=m0, eta=eta, dt=dt, nt=nt, shots=shots, wavelet=wavelet, rec_coords=rec)

@@ -182,3 +182,31 @@ def test_rebind_by_name():
     ref, _, _ = oracle.acoustic_forward(shape, (h,) * 3, (0, 0, 0), 4, m2, eta, dt, 1,
                                         u_cur=u.astype(np.float64), u_prev=u.astype(np.float64))
     assert rel_l2(run.state(1)[0], ref) <= ONE_STEP_TOL
+
+
+def test_tilings_agree_bitwise_and_autotune():
+    """Every tiling (tile height, prefetch depth) computes the same per-point
+    arithmetic, so results agree bit for bit; the autotuner picks one of them."""
+    cfg = wl.acoustic_config(n=72, space_order=8, nt=30, sponge=8, nrec_side=7)
+    args = (cfg["shape"], cfg["spacing"], cfg["origin"], 8, cfg["m"], cfg["eta"], cfg["src_coords"],
+            cfg["src_trace"], cfg["rec_coords"], cfg["nt"])
+    results = []
+    for rows, stages in [(0, 0), (8, 2), (13, 3), (32, 4), (20, 2)]:
+        run = AcousticRun(*args)
+        fd.fd_operator_set_tiling(run.op.handle, rows, stages)
+        r, s, ctas = fd.fd_operator_get_tiling(run.op.handle)
+        assert r > 0 and s >= 2 and ctas > 0
+        if rows:
+            assert r <= rows and s == stages
+        run.run(0, 30, cfg["dt"])
+        results.append((run.state(30)[0], run.rec_trace()))
+    for u, rec in results[1:]:
+        np.testing.assert_array_equal(u, results[0][0])
+        np.testing.assert_array_equal(rec, results[0][1])
+    run = AcousticRun(*args)
+    rows, stages, ms = fd.fd_operator_autotune(run.op.handle, 0, 5, cfg["dt"])
+    assert rows in (8, 10, 12, 14, 16, 18, 20, 24, 27, 32) and 2 <= stages <= 4 and ms > 0
+    with pytest.raises(fd.FDError) as e:
+        fd.fd_operator_set_tiling(run.op.handle, 64, 2)
+    assert e.value.status == fd.FD_ERR_UNSUPPORTED
+    assert fd.fd_operator_get_tiling(run.op.handle)[:2] == (rows, stages)
