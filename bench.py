@@ -285,6 +285,94 @@ def bench_gradient(n=256, nt=1500, k=50, shots=1):
             "grad_rel_diff_vs_plain": rel, "loss": out["tiled"]["loss"]}
 
 
+def bench_batched(nshots=64, nt=800, plain_shots=8):
+    """The batched-shots row: 64 SO8 shots on windows of 160^3-320^3 of a
+    512^3 smooth random model, 800 steps; one launch per step for all shots
+    (eager and as a replayed CUDA graph, tile height autotuned over a short
+    run) against the same shots run one after another with the single-shot
+    tiled operator and with the plain kernels (the latter on `plain_shots`
+    shots, scaled), at equal receiver traces."""
+    import numpy as np
+    import torch
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    cfg = wl.batched_config(nshots=nshots, nt=nt)
+    dt = cfg["dt"]
+    shots = []
+    for i in range(nshots):
+        shape, m, eta, src, rec = wl.window_shot(cfg, i)
+        grid = fd.Grid(shape, cfg["spacing"])
+        u = fd.TimeData("u", grid)
+        md = fd.DenseData("m", grid)
+        ed = fd.DenseData("eta", grid)
+        md.data.copy_(torch.from_numpy(m))
+        ed.data.copy_(torch.from_numpy(eta))
+        sp = fd.PointData("src", grid, src, nt)
+        sp.data[:, :1].copy_(torch.from_numpy(cfg["wavelet"]))
+        rp = fd.PointData("rec", grid, rec, nt)
+        op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, 8, u, md, ed, src=sp, rec=rp)
+        shots.append(dict(grid=grid, u=u, m=md, eta=ed, src=sp, rec=rp, op=op, shape=shape))
+    pts = float(sum(np.prod(s["shape"]) for s in shots)) * nt
+
+    def reset():
+        for s in shots:
+            for t in s["u"].slots:
+                t.zero_()
+
+    def timed(fn):
+        reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    # sequential single-shot runs (each operator's own planner tiling)
+    t_seq = timed(lambda: [s["op"].apply(0, nt, dt) for s in shots])
+    traces_seq = [s["rec"].data[:, :s["rec"].npoint].clone() for s in shots[:plain_shots]]
+    # sequential plain-kernel runs on a subset
+    plain_ops = [fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, 8, s["u"], s["m"], s["eta"], src=s["src"], rec=s["rec"],
+                             flags=fd.FD_FLAG_PLAIN_KERNELS) for s in shots[:plain_shots]]
+    t_plain_sub = timed(lambda: [op.apply(0, nt, dt) for op in plain_ops])
+    traces_plain = [s["rec"].data[:, :s["rec"].npoint].clone() for s in shots[:plain_shots]]
+    pts_sub = float(sum(np.prod(s["shape"]) for s in shots[:plain_shots])) * nt
+    del plain_ops
+    # autotune the batch's tile height and depth on a short run
+    best = None
+    for rows in (8, 12, 16, 20):
+        for stages in (2, 3):
+            try:
+                b = fd.Batch([s["op"] for s in shots], rows=rows, stages=stages)
+            except fd.FDError:
+                continue
+            b.apply(0, 5, dt)
+            b.sync()
+            t = timed(lambda: b.apply(0, 20, dt))
+            if best is None or t < best[0]:
+                best = (t, rows, stages)
+            del b
+    batch = fd.Batch([s["op"] for s in shots], rows=best[1], stages=best[2])
+    info = batch.info()
+    batch.apply(0, 5, dt)
+    batch.sync()
+    t_batch = timed(lambda: batch.apply(0, nt, dt))
+    batch.capture(0, nt, dt)
+    t_graph = timed(lambda: batch.replay())
+    batch.sync()
+    traces_b = [s["rec"].data[:, :s["rec"].npoint] for s in shots[:plain_shots]]
+    err = max(float((a - b).norm() / b.norm()) for a, b in zip(traces_b, traces_plain))
+    err_seq = max(float((a - b).norm() / b.norm()) for a, b in zip(traces_b, traces_seq))
+    return {"workload": "batched_%dshots_windows160-320_of_512^3_so8_nt%d" % (nshots, nt),
+            "value": pts / t_graph / 1e9, "unit": "GPts/s (sum of window points x steps / s)",
+            "s_batch_graph": t_graph, "s_batch_eager": t_batch, "s_sequential_tiled": t_seq,
+            "s_sequential_plain_est": t_plain_sub * pts / pts_sub,
+            "speedup_vs_sequential_plain": (t_plain_sub * pts / pts_sub) / t_graph,
+            "speedup_vs_sequential_tiled": t_seq / t_graph,
+            "trace_rel_diff_vs_plain": err, "trace_rel_diff_vs_sequential_tiled": err_seq,
+            "tiling": {"rows_per_tile": info[0], "prefetch_planes": info[1], "ctas": info[2]},
+            "launches_per_step": 1, "window_points": pts / nt}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -401,7 +489,7 @@ def run_ours(args):
 
     rows = None
     if rank == 0 and not args.no_rows:
-        rows = {"diffusion": bench_diffusion(), "gradient": bench_gradient()}
+        rows = {"diffusion": bench_diffusion(), "gradient": bench_gradient(), "batched": bench_batched()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world, "steps": args.steps,

@@ -307,6 +307,37 @@ fd_status fd_operator_profile(fd_operator *op, int64_t max_launches);
 fd_status fd_operator_profile_read(fd_operator *op, double *total_ms, int64_t *launches);
 
 /* ------------------------------------------------------------------------
+ * Batches of shots
+ * ------------------------------------------------------------------------ */
+
+typedef struct fd_batch fd_batch;
+
+/* Many forward acoustic operators (one per shot, each on its own grid, e.g. a
+ * subgrid window of a larger model: the paper's forward operator applied to a
+ * survey of shots) advanced together, one kernel launch per time step for all
+ * of them.  All operators must be 3D, tiled (not FD_FLAG_PLAIN_KERNELS), not
+ * FD_FLAG_REVERSE, of one space order and grid spacing, on one stream.  The
+ * operators keep their fields, coefficients and traces; the batch sets every
+ * operator's tiling to tiles of at most `rows` rows (0: 16) and sweeps with
+ * `stages` planes prefetched (0: 3).  Rebinding an operator's inputs after
+ * this call requires a new batch.  Errors: FD_ERR_INVALID_ARG,
+ * FD_ERR_UNSUPPORTED, FD_ERR_NOMEM, FD_ERR_CUDA. */
+fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows, int stages, fd_batch **out);
+/* Steps n = t0..t0+nt-1 of every operator (receivers, update, sources as in
+ * fd_operator_apply), enqueued on the operators' stream. */
+fd_status fd_batch_apply(fd_batch *batch, int64_t t0, int64_t nt, double dt);
+/* Capture steps t0..t0+nt-1 once as a CUDA graph (on a private stream; the
+ * coefficients are prepared first, outside the graph), for fd_batch_replay. */
+fd_status fd_batch_capture(fd_batch *batch, int64_t t0, int64_t nt, double dt);
+/* Launch the captured graph on the operators' stream. */
+fd_status fd_batch_replay(fd_batch *batch);
+/* Wait for the stream and report deferred device errors (as fd_operator_sync). */
+fd_status fd_batch_sync(fd_batch *batch);
+/* Tile height, prefetch depth, CTAs per launch, launches so far. */
+fd_status fd_batch_info(const fd_batch *batch, int *rows, int *stages, int *ctas, int64_t *launches);
+void fd_batch_destroy(fd_batch *batch);
+
+/* ------------------------------------------------------------------------
  * Interpolation without allocation (the paper has no counterpart)
  * ------------------------------------------------------------------------ */
 

@@ -602,10 +602,6 @@ static fd_status prepare_coefficients(fd_operator *op, double dt)
     FD_CUDA(launch_coefficients(op->geom, op->m->slot[0], op->eta ? op->eta->slot[0] : nullptr, dt, op->c, op->d, st),
             "coefficients");
     op->launches += 1;
-    if (op->tma.ready) {
-        FD_CUDA(launch_damping_flags(op->tma, st), "damping flags");
-        op->launches += 1;
-    }
     op->coef_dt = dt;
     return FD_OK;
 }
@@ -840,24 +836,15 @@ extern "C" fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stage
     op->tma.force_rows = rows;
     op->tma.force_stages = stages;
     op->tma.cache.clear();
-    // the damping flags are laid out per tile: rebuild them for the new tiling
-    if (op->tma.dflags) {
-        cudaFree(op->tma.dflags);
-        op->tma.dflags = nullptr;
-        op->tma.nz_count = nullptr;
-    }
     fd_status s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
     if (s != FD_OK) {
         op->tma.force_rows = old_rows;
         op->tma.force_stages = old_stages;
         tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
         rebuild_fused(op);
-        op->coef_dt = -1.0;
         return s;
     }
-    s = rebuild_fused(op);
-    op->coef_dt = -1.0;  // recompute the coefficients and the damping flags
-    return s;
+    return rebuild_fused(op);
 }
 
 extern "C" fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, int *stages, int *ctas)
@@ -924,3 +911,191 @@ extern "C" fd_status fd_operator_autotune(fd_operator *op, int64_t t0, int64_t n
     if (best_ms_per_step) *best_ms_per_step = bms;
     return FD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batches of shots
+// ---------------------------------------------------------------------------
+
+struct fd_batch {
+    std::vector<fd_operator *> ops;
+    cudaStream_t stream;
+    cudaStream_t capture_stream;
+    BatchPlan plan;
+    int *status;
+    cudaGraphExec_t graph;
+    bool has_graph;
+    int64_t graph_steps;
+    int64_t launches;
+};
+
+static void batch_release(fd_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->has_graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    batch_plan_release(b->plan);
+    if (b->status) cudaFree(b->status);
+    delete b;
+}
+
+extern "C" fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows, int stages, fd_batch **out)
+{
+    if (!ops || nops < 1 || !out || rows < 0 || stages < 0)
+        return set_error(FD_ERR_INVALID_ARG, "fd_batch_create: bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < nops; i++) {
+        fd_operator *op = ops[i];
+        if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_batch_create: null operator %d", i);
+        if (op->kind != FD_ACOUSTIC_LEAPFROG || op->geom.ndim != 3 || !op->tma.ready)
+            return set_error(FD_ERR_UNSUPPORTED, "fd_batch_create: operator %d is not a tiled 3D acoustic operator", i);
+        if (op->flags & (FD_FLAG_REVERSE | FD_FLAG_PLAIN_KERNELS))
+            return set_error(FD_ERR_UNSUPPORTED, "fd_batch_create: operator %d: forward tiled operators only", i);
+        if (op->so != ops[0]->so || std::memcmp(&op->coef, &ops[0]->coef, sizeof(Coef)) != 0)
+            return set_error(FD_ERR_UNSUPPORTED, "fd_batch_create: operators differ in space order or spacing");
+        if (op->stream != ops[0]->stream)
+            return set_error(FD_ERR_INVALID_ARG, "fd_batch_create: operators on different streams");
+    }
+    const int want_stages = stages > 0 ? stages : 3;
+    const int want_rows = rows > 0 ? rows : 16;
+    for (int i = 0; i < nops; i++) {
+        fd_status s = fd_operator_set_tiling(ops[i], want_rows, 0);
+        if (s != FD_OK) return s;
+        if (ops[i]->src && ops[i]->src->npoint > 0 && !ops[i]->tma.has_src)
+            return set_error(FD_ERR_UNSUPPORTED, "fd_batch_create: operator %d's sources do not fit the tiles", i);
+    }
+    fd_batch *b = new (std::nothrow) fd_batch();
+    if (!b) return set_error(FD_ERR_NOMEM, "fd_batch_create: out of host memory");
+    b->ops.assign(ops, ops + nops);
+    b->stream = ops[0]->stream;
+    b->capture_stream = nullptr;
+    b->status = nullptr;
+    b->has_graph = false;
+    b->graph_steps = 0;
+    b->launches = 0;
+    std::vector<const TmaPlan *> plans;
+    std::vector<const SparseDev *> recs;
+    std::vector<float *> rtr;
+    std::vector<long long> rst, sst;
+    std::vector<const float *> str;
+    for (fd_operator *op : b->ops) {
+        plans.push_back(&op->tma);
+        const bool hr = op->rec && op->rec->npoint > 0, hs = op->src && op->src->npoint > 0;
+        recs.push_back(hr ? &op->rec->dev : nullptr);
+        rtr.push_back(hr ? op->rec->trace : nullptr);
+        rst.push_back(hr ? op->rec->stride : 0);
+        str.push_back(hs ? op->src->trace : nullptr);
+        sst.push_back(hs ? op->src->stride : 0);
+    }
+    fd_status s = batch_plan_build(b->plan, plans, recs, rtr, rst, str, sst, ops[0]->coef, want_stages, b->stream);
+    if (s != FD_OK) {
+        batch_release(b);
+        return s;
+    }
+    cudaError_t e = cudaMalloc((void **)&b->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        batch_release(b);
+        return cuda_error(e, "fd_batch_create");
+    }
+    *out = b;
+    return FD_OK;
+}
+
+// Validate a run of the batch and prepare every operator's coefficients.
+static fd_status batch_prepare(fd_batch *b, int64_t t0, int64_t nt, double dt, const char *who)
+{
+    if (nt < 0 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "%s: need t0 >= 0, nt >= 0", who);
+    for (fd_operator *op : b->ops) {
+        for (fd_sparse *sp : {op->src, op->rec})
+            if (sp && sp->npoint > 0 && t0 + nt > sp->nt)
+                return set_error(FD_ERR_INVALID_ARG, "%s: a trace has %lld rows, need %lld", who, (long long)sp->nt,
+                                 (long long)(t0 + nt));
+        fd_status s = check_dt(op, dt, who);
+        if (s != FD_OK) return s;
+        s = prepare_coefficients(op, dt);
+        if (s != FD_OK) return s;
+    }
+    return FD_OK;
+}
+
+static fd_status batch_enqueue(fd_batch *b, int64_t t0, int64_t nt, cudaStream_t st)
+{
+    for (int64_t n = t0; n < t0 + nt; n++) {
+        FD_CUDA(launch_batch(b->plan, (long long)n, (int)(n & 1), b->status, st), "batch step");
+        b->launches += 1;
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_apply(fd_batch *b, int64_t t0, int64_t nt, double dt)
+{
+    if (!b) return set_error(FD_ERR_INVALID_ARG, "fd_batch_apply: null batch");
+    fd_status s = batch_prepare(b, t0, nt, dt, "fd_batch_apply");
+    if (s != FD_OK) return s;
+    return batch_enqueue(b, t0, nt, b->stream);
+}
+
+extern "C" fd_status fd_batch_capture(fd_batch *b, int64_t t0, int64_t nt, double dt)
+{
+    if (!b || nt < 1) return set_error(FD_ERR_INVALID_ARG, "fd_batch_capture: bad arguments");
+    fd_status s = batch_prepare(b, t0, nt, dt, "fd_batch_capture");
+    if (s != FD_OK) return s;
+    FD_CUDA(cudaStreamSynchronize(b->stream), "fd_batch_capture");
+    if (b->has_graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->has_graph = false;
+    }
+    FD_CUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "fd_batch_capture: begin");
+    const int64_t before = b->launches;
+    s = batch_enqueue(b, t0, nt, b->capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->capture_stream, &graph);
+    b->launches = before;  // captured launches run at replay
+    if (s != FD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "fd_batch_capture: end");
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_error(e, "fd_batch_capture: instantiate");
+    b->has_graph = true;
+    b->graph_steps = nt;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_replay(fd_batch *b)
+{
+    if (!b || !b->has_graph) return set_error(FD_ERR_INVALID_ARG, "fd_batch_replay: nothing captured");
+    FD_CUDA(cudaGraphLaunch(b->graph, b->stream), "fd_batch_replay");
+    b->launches += b->graph_steps;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_sync(fd_batch *b)
+{
+    if (!b) return set_error(FD_ERR_INVALID_ARG, "fd_batch_sync: null batch");
+    FD_CUDA(cudaStreamSynchronize(b->stream), "fd_batch_sync");
+    int status = 0;
+    FD_CUDA(cudaMemcpy(&status, b->status, sizeof status, cudaMemcpyDeviceToHost), "fd_batch_sync: status");
+    if (status != 0) {
+        cudaMemset(b->status, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        return set_error(FD_ERR_TIMEOUT, "fd_batch_sync: a device wait gave up (code %d)", status);
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_info(const fd_batch *b, int *rows, int *stages, int *ctas, int64_t *launches)
+{
+    if (!b) return set_error(FD_ERR_INVALID_ARG, "fd_batch_info: null batch");
+    if (rows) *rows = b->plan.rows_max;
+    if (stages) *stages = b->plan.P;
+    if (ctas) *ctas = b->plan.nctas;
+    if (launches) *launches = b->launches;
+    return FD_OK;
+}
+
+extern "C" void fd_batch_destroy(fd_batch *b) { batch_release(b); }

@@ -63,11 +63,6 @@ struct TmaPlan {
     CUtensorMap u_tile[2];   // slot s of u, tile box (kTileW x rows_max x 1)
     CUtensorMap c_tile, d_tile;
     float *slot[2] = {nullptr, nullptr};
-    const float *d = nullptr;
-    // per (tile, d0 plane): 1 if d = dt*eta/m is non-zero somewhere on it, so
-    // the kernel skips the d box of all-zero blocks (outside the sponge)
-    unsigned char *dflags = nullptr;
-    unsigned long long *nz_count = nullptr;  // grid points with d != 0
     // fused receiver interpolation / source injection (library-owned)
     SparseFused fused;
     void *fused_mem = nullptr;
@@ -91,8 +86,6 @@ void tma_plan_release(TmaPlan &plan, cudaStream_t st);
 // Tile height and prefetch depth of a built plan (for reporting).
 void tma_plan_tiling(const TmaPlan &plan, int *rows, int *stages, int *ctas);
 
-// Recompute plan.dflags (and the non-zero count) from the d field; enqueue on st.
-cudaError_t launch_damping_flags(const TmaPlan &plan, cudaStream_t st);
 
 // One acoustic step between arbitrary buffers: reads u_cur (haloed) and
 // u_prev, writes u_next (may equal u_prev).  Tensor maps are encoded on first
@@ -110,5 +103,30 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
 // given and the plan fuses the sources.
 cudaError_t launch_acoustic_tma(const TmaPlan &plan, int M, const Geom &g, const Coef &cf,
                                 int cur, int *status, const float *src_row, cudaStream_t st);
+
+// ---- many shots per launch (k_batch.cu) ----------------------------------
+
+struct ShotDesc;
+struct BatchItem;
+
+struct BatchPlan {
+    int M = 0, P = 0, rows_max = 0, src_cap = 0, nctas = 0, threads = 0;
+    size_t smem = 0;
+    Coef cf{};
+    ShotDesc *d_shots = nullptr;
+    BatchItem *d_items = nullptr;
+    int *d_off = nullptr;
+};
+
+// Build the device tables of a batch from the shots' tiled plans (all of the
+// same space order and coefficients), their receivers and traces.
+fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &plans,
+                           const std::vector<const SparseDev *> &recs, const std::vector<float *> &rec_traces,
+                           const std::vector<long long> &rec_strides, const std::vector<const float *> &src_traces,
+                           const std::vector<long long> &src_strides, const Coef &cf, int stages,
+                           cudaStream_t st);
+void batch_plan_release(BatchPlan &bp);
+// One time step n of every shot: reads slot `cur`, writes slot cur^1.
+cudaError_t launch_batch(const BatchPlan &bp, long long n, int cur, int *status, cudaStream_t st);
 
 }  // namespace fdgb

@@ -1,0 +1,357 @@
+// Device side of the tiled acoustic kernels: PTX helpers and the sweep of
+// one tile column, shared by the single-grid kernel (k_tma.cu) and the
+// batched many-shot kernel (k_batch.cu).
+//
+// A tile column is rows [row0, row0+rows) of d1 and 64 columns of d2 of one
+// grid, swept over every d0 plane:
+//   * one TMA box brings the haloed u^n tile (64+16 columns, rows+2M rows)
+//     into a ring of shared-memory planes; the zero halo around the grid is
+//     the TMA out-of-bounds fill, so no halo is stored in HBM;
+//   * three TMA boxes bring u^{n-1}, c = dt^2/m and d = dt*eta/m of the plane
+//     being finished into a second ring;
+//   * every thread owns 4 consecutive d2 points of one row, keeps the 2M+1
+//     centre values along d0 in a register queue, reads the d1/d2 neighbours
+//     of the plane M behind the newest from shared memory, adds the source
+//     injection of the corners it owns and writes u^{n+1} with 128-bit stores.
+// One elected thread issues the copies P planes ahead on mbarriers with
+// transaction counts; every wait is bounded by the global timer and, when it
+// gives up, the CTA records FD_ERR_TIMEOUT in the status word and leaves after
+// draining its own copies.
+#pragma once
+
+#include "fd_tma.h"
+
+namespace fdgb {
+
+namespace tile_dev {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of a barrier, giving up after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(map)) : "memory");
+}
+
+__host__ __device__ constexpr int round_up32(int x) { return (x + 31) / 32 * 32; }
+
+// floats of one ring plane (rounded so every plane starts 128-byte aligned)
+__host__ __device__ inline int ring_plane_floats(int box_h) { return round_up32(box_h * kBoxW); }
+
+// Shared memory of the tiled kernel: the u^n ring, the aux ring, the
+// mbarriers and the abort flag; then room for src_cap injected corners of the
+// tile and their per-plane starts.
+__host__ __device__ inline size_t tma_smem_core(int M, int P, int rows_max)
+{
+    const int NU = M + 1 + P, NA = P + 1;
+    const int box_h = rows_max + 2 * M;
+    return sizeof(float) * ((size_t)NU * ring_plane_floats(box_h) + (size_t)NA * 3 * rows_max * kTileW) +
+           sizeof(unsigned long long) * (NU + NA) + 16;
+}
+
+__host__ __device__ inline size_t tma_smem_bytes(int M, int P, int rows_max, int n0, int src_cap)
+{
+    return tma_smem_core(M, P, rows_max) + sizeof(SrcEntry) * (size_t)src_cap + sizeof(int) * (size_t)(n0 + 1);
+}
+
+
+// Shared-memory areas of a tiled CTA (sized for the largest column it sweeps).
+struct SweepSmem {
+    float *ring;                 // NU planes of plane_u floats
+    float *aux;                  // NA slots of 3 boxes of plane_a floats
+    unsigned long long *bars;    // NU + NA mbarriers
+    volatile int *abort;
+    SrcEntry *src;               // the column's injected corners
+    int *sstart;                 // per-plane starts into src
+    int plane_u, plane_a;
+};
+
+// Carve the dynamic shared memory of a CTA whose columns have at most
+// rows_max rows, n0_max planes and src_cap injected corners.
+template <int M, int P>
+__device__ inline SweepSmem carve_smem(unsigned char *raw, int rows_max, int src_cap)
+{
+    constexpr int NU = M + 1 + P, NA = P + 1;
+    SweepSmem sm;
+    sm.plane_u = ring_plane_floats(rows_max + 2 * M);
+    sm.plane_a = rows_max * kTileW;
+    sm.ring = reinterpret_cast<float *>(raw);
+    sm.aux = sm.ring + NU * sm.plane_u;
+    sm.bars = reinterpret_cast<unsigned long long *>(sm.aux + NA * 3 * sm.plane_a);
+    sm.abort = reinterpret_cast<volatile int *>(sm.bars + NU + NA);
+    sm.src = reinterpret_cast<SrcEntry *>(sm.bars + NU + NA) + 1;
+    sm.sstart = reinterpret_cast<int *>(sm.src + src_cap);
+    return sm;
+}
+
+template <int M, int P>
+__device__ inline void init_barriers(const SweepSmem &sm)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < M + 1 + P + P + 1; i++) mbar_init(smem_addr(&sm.bars[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *sm.abort = 0;
+    }
+    __syncthreads();
+}
+
+// Sweep tile `tile` of one grid.  it_u / it_a count the u^n and aux loads this
+// CTA has consumed so far (ring slots and barrier phases continue across
+// columns).  Returns false when a wait gave up (status set, copies drained).
+template <int M, int P>
+__device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
+                             const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
+                             int tile, const SrcEntry *__restrict__ src_tab, int nsrc,
+                             const float *__restrict__ src_row, const SweepSmem &sm, unsigned &it_u, unsigned &it_a,
+                             int *status)
+{
+    constexpr int NU = M + 1 + P;     // u^n planes alive: M behind the newest, the newest, P in flight
+    constexpr int NA = P + 1;         // aux planes (u^{n-1}, c, d)
+    constexpr int HV = (M + 3) / 4;   // float4 groups on each side of a thread's 4 points
+    constexpr int NR = 4 * (2 * HV + 1);
+    constexpr int Q = 2 * M + 1;      // d0 queue length
+
+    const int tid = threadIdx.x;
+    const int strip = tile / a.k2;
+    const int tile2 = tile - strip * a.k2;
+    const int row0 = (int)((long long)strip * a.n1 / a.k1);
+    const int rows = (int)((long long)(strip + 1) * a.n1 / a.k1) - row0;
+    const int col0 = tile2 * kTileW;
+    const int r = tid >> 4;
+    const int qc = tid & 15;
+    const bool active = r < rows && col0 + 4 * qc < a.n2;
+    const int J = a.n0 + 2 * M;
+    const int plane_u = sm.plane_u, plane_a = sm.plane_a;
+    float *ring = sm.ring;
+    float *aux = sm.aux;
+    unsigned long long *bars = sm.bars;
+    const uint32_t bytes_u = (uint32_t)(kBoxW * a.box_h * sizeof(float));
+    const uint32_t bytes_a = (uint32_t)(3 * a.rows_max * kTileW * sizeof(float));
+    const unsigned iu = it_u, ia = it_a;
+
+    // iteration j: u^n plane j-M into ring slot (iu+j) % NU; for j >= 2M the
+    // aux of output plane j-2M into aux slot (ia+j-2M) % NA
+    auto issue = [&](int j) {
+        const unsigned gu = iu + (unsigned)j;
+        const int su = (int)(gu % NU);
+        const uint32_t bu = smem_addr(&bars[su]);
+        mbar_expect_tx(bu, bytes_u);
+        tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, j - M, bu);
+        if (j >= 2 * M) {
+            const int ja = j - 2 * M;
+            const int sa = (int)((ia + (unsigned)ja) % NA);
+            const uint32_t ba = smem_addr(&bars[NU + sa]);
+            float *dst = aux + sa * 3 * plane_a;
+            mbar_expect_tx(ba, bytes_a);
+            tma_load_3d(smem_addr(dst), map_um, col0, row0, ja, ba);
+            tma_load_3d(smem_addr(dst + plane_a), map_c, col0, row0, ja, ba);
+            tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, ja, ba);
+        }
+    };
+    auto wait_u = [&](int j) {
+        const unsigned gu = iu + (unsigned)j;
+        return mbar_wait_bounded(smem_addr(&bars[gu % NU]), (uint32_t)((gu / NU) & 1));
+    };
+    auto wait_a = [&](int ja) {
+        const unsigned ga = ia + (unsigned)ja;
+        return mbar_wait_bounded(smem_addr(&bars[NU + ga % NA]), (uint32_t)((ga / NA) & 1));
+    };
+
+    if (tid == 0)
+        for (int j = 0; j < P && j < J; j++) issue(j);
+
+    // the column's injected corners, staged in shared memory so that the
+    // plane loop never waits on them
+    SrcEntry *s_src = sm.src;
+    int *s_sstart = sm.sstart;
+    if (!src_row) nsrc = 0;
+    for (int q = tid; q < nsrc * 5; q += blockDim.x)
+        reinterpret_cast<int *>(s_src)[q] = reinterpret_cast<const int *>(src_tab)[q];
+    __syncthreads();
+    if (nsrc > 0) {
+        for (int z = tid; z <= a.n0; z += blockDim.x) {
+            int lo = 0, hi = nsrc;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_src[mid].z < z) lo = mid + 1; else hi = mid;
+            }
+            s_sstart[z] = lo;
+        }
+        __syncthreads();
+    }
+
+    // d0 queue: q[k] holds the thread's 4 centre values of plane z - M + k
+    // for the output plane z of the current iteration (shifted each plane)
+    float4 q[Q];
+#pragma unroll
+    for (int k = 0; k < Q; k++) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    int j = 0;
+    bool ok = true, stop = false;
+    for (; j < J; j++) {
+        if (tid == 0 && j + P < J) issue(j + P);
+        ok = wait_u(j) && ok;
+#pragma unroll
+        for (int k = 0; k < Q - 1; k++) q[k] = q[k + 1];
+        q[Q - 1] = *reinterpret_cast<const float4 *>(ring + ((iu + j) % NU) * plane_u + (r + M) * kBoxW + kSideHalo +
+                                                     4 * qc);
+        if (j >= 2 * M) {
+            const int ja = j - 2 * M;  // output plane
+            ok = wait_a(ja) && ok;
+            if (ok && active) {
+                const float *pc =
+                    ring + ((iu + j - M) % NU) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc;
+                float row[NR];
+#pragma unroll
+                for (int v = 0; v < 2 * HV + 1; v++) {
+                    float4 t = *reinterpret_cast<const float4 *>(pc + 4 * (v - HV));
+                    row[4 * v + 0] = t.x;
+                    row[4 * v + 1] = t.y;
+                    row[4 * v + 2] = t.z;
+                    row[4 * v + 3] = t.w;
+                }
+                float4 cm[M + 1], cp[M + 1];
+#pragma unroll
+                for (int k = 1; k <= M; k++) {
+                    cm[k] = *reinterpret_cast<const float4 *>(pc - k * kBoxW);
+                    cp[k] = *reinterpret_cast<const float4 *>(pc + k * kBoxW);
+                }
+                const float *pa = aux + ((ia + ja) % NA) * 3 * plane_a + r * kTileW + 4 * qc;
+                const float4 um4 = *reinterpret_cast<const float4 *>(pa);
+                const float4 c4 = *reinterpret_cast<const float4 *>(pa + plane_a);
+                const float4 d4 = *reinterpret_cast<const float4 *>(pa + 2 * plane_a);
+                const float umv[4] = {um4.x, um4.y, um4.z, um4.w};
+                const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+                float res[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float u = row[4 * HV + i];
+                    float lap = cf.centre * u;
+#pragma unroll
+                    for (int k = 1; k <= M; k++) {
+                        const float4 lo = q[M - k];
+                        const float4 hi = q[M + k];
+                        const float s2 = row[4 * HV + i - k] + row[4 * HV + i + k];
+                        const float s1 = (&cm[k].x)[i] + (&cp[k].x)[i];
+                        const float s0 = (&lo.x)[i] + (&hi.x)[i];
+                        lap = fmaf(cf.ax[2][k], s2, lap);
+                        lap = fmaf(cf.ax[1][k], s1, lap);
+                        lap = fmaf(cf.ax[0][k], s0, lap);
+                    }
+                    res[i] = 2.0f * u - umv[i] + cv[i] * lap - dv[i] * (u - umv[i]);
+                }
+                if (nsrc > 0) {
+                    // source injection at the corners this thread owns on plane ja
+                    float inj0 = 0.f, inj1 = 0.f, inj2 = 0.f, inj3 = 0.f;
+                    const int s_end = s_sstart[ja + 1];
+                    for (int k = s_sstart[ja]; k < s_end; k++) {
+                        const SrcEntry e = s_src[k];
+                        if (e.r == r && (e.x >> 2) == qc) {
+                            const float sv = e.w * src_row[e.p];
+                            const int i = e.x & 3;
+                            inj0 += (i == 0) ? sv : 0.f;
+                            inj1 += (i == 1) ? sv : 0.f;
+                            inj2 += (i == 2) ? sv : 0.f;
+                            inj3 += (i == 3) ? sv : 0.f;
+                        }
+                    }
+                    res[0] = fmaf(inj0, cv[0], res[0]);
+                    res[1] = fmaf(inj1, cv[1], res[1]);
+                    res[2] = fmaf(inj2, cv[2], res[2]);
+                    res[3] = fmaf(inj3, cv[3], res[3]);
+                }
+                float *o = out + (long long)ja * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
+                if (col0 + 4 * qc + 3 < a.n2) {
+                    *reinterpret_cast<float4 *>(o) = make_float4(res[0], res[1], res[2], res[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        if (col0 + 4 * qc + i < a.n2) o[i] = res[i];
+                }
+            }
+        }
+        if (!ok) *sm.abort = 1;
+        __syncthreads();
+        if (*sm.abort) {
+            stop = true;
+            break;
+        }
+    }
+
+    if (stop) {
+        // a wait gave up: record it, then drain this CTA's copies still in
+        // flight (issued up to min(j+P, J-1)) before leaving
+        if (tid == 0) {
+            atomicExch(status, (int)FD_ERR_TIMEOUT);
+            const int last = (j + P < J) ? j + P : J - 1;
+            for (int i = j; i <= last; i++) {
+                if (!wait_u(i)) break;
+                if (i >= 2 * M && !wait_a(i - 2 * M)) break;
+            }
+        }
+        __syncthreads();
+        return false;
+    }
+    it_u = iu + (unsigned)J;
+    it_a = ia + (unsigned)a.n0;
+    return true;
+}
+
+}  // namespace tile_dev
+
+}  // namespace fdgb

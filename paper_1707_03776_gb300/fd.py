@@ -80,6 +80,15 @@ _SIGNATURES = [
     ("fd_operator_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     ("fd_operator_autotune", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _c_f64p]),
+    ("fd_batch_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(_vp)]),
+    ("fd_batch_apply", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]),
+    ("fd_batch_capture", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]),
+    ("fd_batch_replay", ctypes.c_int, [_vp]),
+    ("fd_batch_sync", ctypes.c_int, [_vp]),
+    ("fd_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), _c_i64p]),
+    ("fd_batch_destroy", None, [_vp]),
     ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -280,6 +289,39 @@ def fd_operator_get_tiling(op):
     return r.value, s.value, c.value
 
 
+def fd_batch_create(op_handles, rows=0, stages=0):
+    arr = (_vp * len(op_handles))(*[h.value if isinstance(h, _vp) else h for h in op_handles])
+    h = _vp()
+    _check(lib().fd_batch_create(arr, len(op_handles), int(rows), int(stages), ctypes.byref(h)))
+    return h
+
+
+def fd_batch_apply(b, t0, nt, dt):
+    _check(lib().fd_batch_apply(b, int(t0), int(nt), float(dt)))
+
+
+def fd_batch_capture(b, t0, nt, dt):
+    _check(lib().fd_batch_capture(b, int(t0), int(nt), float(dt)))
+
+
+def fd_batch_replay(b):
+    _check(lib().fd_batch_replay(b))
+
+
+def fd_batch_sync(b):
+    _check(lib().fd_batch_sync(b))
+
+
+def fd_batch_info(b):
+    r, s, c, n = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int64(0)
+    _check(lib().fd_batch_info(b, ctypes.byref(r), ctypes.byref(s), ctypes.byref(c), ctypes.byref(n)))
+    return r.value, s.value, c.value, n.value
+
+
+def fd_batch_destroy(b):
+    lib().fd_batch_destroy(b)
+
+
 def fd_interpolate_noalloc(grid, coords, dev_field, dev_out, stream=0):
     """Interpolate a device field slot at host coordinates into dev_out
     without any allocation (see include/fd.h)."""
@@ -378,6 +420,34 @@ class PointData:
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
             fd_sparse_destroy(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """Many forward operators (shots) advanced with one launch per step."""
+
+    def __init__(self, operators, rows=0, stages=0):
+        self._ops = list(operators)
+        self.handle = fd_batch_create([o.handle for o in self._ops], rows, stages)
+
+    def apply(self, t0, nt, dt):
+        fd_batch_apply(self.handle, t0, nt, dt)
+
+    def capture(self, t0, nt, dt):
+        fd_batch_capture(self.handle, t0, nt, dt)
+
+    def replay(self):
+        fd_batch_replay(self.handle)
+
+    def sync(self):
+        fd_batch_sync(self.handle)
+
+    def info(self):
+        return fd_batch_info(self.handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            fd_batch_destroy(self.handle)
             self.handle = None
 
 

@@ -200,3 +200,54 @@ def gradient_config(n=256, nt=1500, nshots=8, nrec_side=65, h=10.0, space_order=
     wavelet = ricker(nt, dt, f0).astype(np.float32).reshape(nt, 1)
     return dict(shape=shape, spacing=spacing, origin=(0.0, 0.0, 0.0), space_order=space_order, m_true=m_true,
                 m0=m0, eta=eta, dt=dt, nt=nt, shots=shots, wavelet=wavelet, rec_coords=rec)
+
+
+def batched_config(nshots=64, n_model=512, wmin=160, wmax=320, nt=800, h=10.0, sponge=20, nrec_side=32,
+                   f0=10.0, seed=3):
+    """Batched-shots workload: a seeded n_model^3 smooth random velocity model
+    (Gaussian-filtered noise, sigma 8 cells, 1.5-4.5 km/s, FP32), and `nshots`
+    subgrid windows with per-axis sizes uniform in [wmin, wmax] and origins
+    uniform such that each window fits.  Every shot has one Ricker source at
+    its window's surface centre (depth index `sponge`) and nrec_side^2
+    receivers half a cell below; its own `sponge`-cell sponge at the window's
+    faces; dt at CFL 0.4 of 4.5 km/s.  Returns the model (FP32 velocity) and a
+    list of windows (origin, shape)."""
+    g = np.random.default_rng(SEED_BASE + 4242 * seed)
+    shape = (n_model,) * 3
+    u = g.standard_normal(shape, dtype=np.float32)
+    for a in range(3):
+        k = np.fft.rfftfreq(n_model).astype(np.float32)
+        filt = np.exp(-0.5 * (2 * math.pi * k * 8.0) ** 2).astype(np.float32)
+        sh = [1, 1, 1]
+        sh[a] = filt.size
+        u = np.fft.irfft(np.fft.rfft(u, axis=a) * filt.reshape(sh), n=n_model, axis=a).astype(np.float32)
+    lo, hi = float(u.min()), float(u.max())
+    v = (1500.0 + 3000.0 * (u - lo) / (hi - lo)).astype(np.float32)
+    windows = []
+    for _ in range(nshots):
+        wshape = tuple(int(x) for x in g.integers(wmin, wmax + 1, size=3))
+        origin = tuple(int(g.integers(0, n_model - w + 1)) for w in wshape)
+        windows.append((origin, wshape))
+    dt = 0.4 * h / 4500.0
+    wavelet = ricker(nt, dt, f0).astype(np.float32).reshape(nt, 1)
+    return dict(velocity=v, windows=windows, spacing=(h, h, h), dt=dt, nt=nt, sponge=sponge,
+                nrec_side=nrec_side, wavelet=wavelet, v_max=4500.0)
+
+
+def window_shot(cfg, i):
+    """Inputs of shot i of a batched_config: m, eta (FP32 window fields),
+    source and receiver coordinates in the window's own frame."""
+    (o0, o1, o2), shape = cfg["windows"][i]
+    v = cfg["velocity"][o0:o0 + shape[0], o1:o1 + shape[1], o2:o2 + shape[2]].astype(np.float64)
+    m = (1.0 / v ** 2).astype(np.float32)
+    sigma = sponge_sigma(shape, cfg["spacing"], cfg["sponge"], cfg["v_max"], ref_width=40)
+    eta = (m.astype(np.float64) * sigma).astype(np.float32)
+    h = cfg["spacing"][0]
+    depth = float(cfg["sponge"])
+    src = np.array([[(shape[0] - 1) / 2.0 * h, (shape[1] - 1) / 2.0 * h, depth * h]])
+    n = cfg["nrec_side"]
+    gx = np.linspace(depth, shape[0] - 1 - depth, n)
+    gy = np.linspace(depth, shape[1] - 1 - depth, n)
+    X, Y = np.meshgrid(gx, gy, indexing="ij")
+    rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, depth + 0.5)], axis=1) * h
+    return shape, m, eta, src, rec
