@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-rows", action="store_true", help="skip the secondary rows (2D diffusion)")
     p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
+    p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel (default: autotuned)")
     return p.parse_args()
 
 
@@ -400,7 +401,12 @@ def run_ours(args):
     src_h = torch.from_numpy(cfg["src_trace"]).pin_memory()
     model.load(m_h, eta_h, src_h)
     tiling = None
-    if not args.plain:
+    if not args.plain and args.tiling:
+        rows, stages = (int(x) for x in args.tiling.split(","))
+        fd.fd_operator_set_tiling(model.op.handle, rows, stages)
+        r, s_, ctas = fd.fd_operator_get_tiling(model.op.handle)
+        tiling = {"rows_per_tile": r, "prefetch_planes": s_, "ctas": ctas, "source": "--tiling"}
+    elif not args.plain:
         rows, stages, ms_tuned = model.autotune(cfg["dt"])
         tiling = {"rows_per_tile": rows, "prefetch_planes": stages, "autotuned_ms_per_step": ms_tuned,
                   "ctas": fd.fd_operator_get_tiling(model.op.handle)[2]}
