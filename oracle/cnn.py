@@ -1,0 +1,100 @@
+"""CPU oracle for the learned closure's 3D CNN (test infrastructure only).
+
+Plain FP64 numpy restatement of what the closure network computes; the CUDA
+implicit-GEMM kernels are checked against it.  Only the test suite and the
+benchmark may import it.
+
+Conventions (channels-last, as the device stores activations):
+  x   [n0, n1, n2, C_in]           input field
+  w   [27, C_in, C_out]            kernel taps; tap t = (a+1)*9 + (b+1)*3 + (c+1)
+                                   for offsets a, b, c in {-1, 0, 1}
+  b   [C_out]                      bias
+  y[i,j,k,o] = b[o] + sum_t sum_c w[t, c, o] x[i+a, j+b, k+c, c]
+  with x = 0 outside the grid (zero padding, output the same size): a
+  3x3x3 cross-correlation.
+
+The network: conv(C0 -> 16) ReLU, conv(16 -> 16) ReLU, conv(16 -> 16) ReLU,
+conv(16 -> 1); the closure adds its output to the coarse update.
+"""
+import numpy as np
+
+TAPS = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+
+
+def _shift(x, a, b, c):
+    """x shifted so that out[i,j,k] = x[i+a, j+b, k+c], zero outside."""
+    out = np.zeros_like(x)
+    n0, n1, n2 = x.shape[:3]
+    src = (slice(max(a, 0), n0 + min(a, 0)), slice(max(b, 0), n1 + min(b, 0)), slice(max(c, 0), n2 + min(c, 0)))
+    dst = (slice(max(-a, 0), n0 + min(-a, 0)), slice(max(-b, 0), n1 + min(-b, 0)),
+           slice(max(-c, 0), n2 + min(-c, 0)))
+    out[dst] = x[src]
+    return out
+
+
+def conv3d(x, w, b):
+    """y = b + sum over taps of shifted x times the tap's C_in x C_out matrix."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    y = np.zeros(x.shape[:3] + (w.shape[2],), dtype=np.float64)
+    y += np.asarray(b, dtype=np.float64)
+    for t, (a, bb, c) in enumerate(TAPS):
+        y += _shift(x, a, bb, c) @ w[t]
+    return y
+
+
+def conv3d_grad_input(gy, w):
+    """dL/dx for y = conv3d(x, w, b): gx[p] = sum_t w[t] gy[p - offset_t]."""
+    gy = np.asarray(gy, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    gx = np.zeros(gy.shape[:3] + (w.shape[1],), dtype=np.float64)
+    for t, (a, bb, c) in enumerate(TAPS):
+        gx += _shift(gy, -a, -bb, -c) @ w[t].T
+    return gx
+
+
+def conv3d_grad_weight(x, gy):
+    """(dL/dw, dL/db): gw[t] = sum_p x[p + offset_t]^T gy[p], gb = sum_p gy[p]."""
+    x = np.asarray(x, dtype=np.float64)
+    gy = np.asarray(gy, dtype=np.float64)
+    cin, cout = x.shape[3], gy.shape[3]
+    gw = np.zeros((27, cin, cout), dtype=np.float64)
+    G = gy.reshape(-1, cout)
+    for t, (a, bb, c) in enumerate(TAPS):
+        gw[t] = _shift(x, a, bb, c).reshape(-1, cin).T @ G
+    return gw, G.sum(axis=0)
+
+
+def network_forward(x, params):
+    """Activations of the 4-layer network; params = [(w, b)] * 4."""
+    acts = [np.asarray(x, dtype=np.float64)]
+    pre = []
+    h = acts[0]
+    for li, (w, b) in enumerate(params):
+        z = conv3d(h, w, b)
+        pre.append(z)
+        h = np.maximum(z, 0.0) if li < len(params) - 1 else z
+        acts.append(h)
+    return acts, pre
+
+
+def network_backward(acts, pre, params, gout):
+    """Gradients of a scalar loss with dL/d(output) = gout: [(gw, gb)] per layer."""
+    grads = [None] * len(params)
+    g = np.asarray(gout, dtype=np.float64)
+    for li in range(len(params) - 1, -1, -1):
+        if li < len(params) - 1:
+            g = g * (pre[li] > 0.0)
+        gw, gb = conv3d_grad_weight(acts[li], g)
+        grads[li] = (gw, gb)
+        g = conv3d_grad_input(g, params[li][0])
+    return grads
+
+
+def bf16_round(a):
+    """Round FP32 values to the nearest BF16 (ties to even), returned as FP32."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).reshape(a.shape)

@@ -1,0 +1,103 @@
+"""Pins of the closure network's CPU oracle (CPU only).
+
+  * conv3d equals a brute-force loop over points, taps and channels, and a
+    single-channel conv equals scipy.ndimage.correlate with zero padding;
+  * input and weight gradients of conv3d equal central finite differences of
+    a random linear functional (FP64);
+  * the whole network's parameter gradients equal finite differences;
+  * bf16_round matches the round-to-nearest-even definition on edge cases.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+
+def _rand(shape, seed):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+def test_conv_bruteforce():
+    x = _rand((5, 4, 6, 3), 1)
+    w = _rand((27, 3, 2), 2)
+    b = _rand((2,), 3)
+    y = cnn.conv3d(x, w, b)
+    ref = np.zeros((5, 4, 6, 2))
+    for i, j, k in itertools.product(range(5), range(4), range(6)):
+        acc = b.copy()
+        for t, (a, bb, c) in enumerate(cnn.TAPS):
+            ii, jj, kk = i + a, j + bb, k + c
+            if 0 <= ii < 5 and 0 <= jj < 4 and 0 <= kk < 6:
+                acc += x[ii, jj, kk] @ w[t]
+        ref[i, j, k] = acc
+    np.testing.assert_allclose(y, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_conv_single_channel_is_correlate():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    x = _rand((7, 8, 9), 4)
+    k = _rand((3, 3, 3), 5)
+    w = k.reshape(27, 1, 1)
+    y = cnn.conv3d(x[..., None], w, np.zeros(1))[..., 0]
+    ref = ndimage.correlate(x, k, mode="constant", cval=0.0)
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_conv_gradients_match_finite_differences():
+    x = _rand((4, 5, 3, 2), 6)
+    w = _rand((27, 2, 3), 7)
+    b = _rand((3,), 8)
+    R = _rand((4, 5, 3, 3), 9)  # L = sum(R * y)
+    gx = cnn.conv3d_grad_input(R, w)
+    gw, gb = cnn.conv3d_grad_weight(x, R)
+    L = lambda xx, ww, bbb: float((R * cnn.conv3d(xx, ww, bbb)).sum())  # noqa: E731
+    eps = 1e-6
+    g = np.random.default_rng(10)
+    for _ in range(3):
+        dx = g.standard_normal(x.shape)
+        fd = (L(x + eps * dx, w, b) - L(x - eps * dx, w, b)) / (2 * eps)
+        assert abs(fd - float((gx * dx).sum())) < 1e-7 * max(1.0, abs(fd))
+        dw = g.standard_normal(w.shape)
+        fd = (L(x, w + eps * dw, b) - L(x, w - eps * dw, b)) / (2 * eps)
+        assert abs(fd - float((gw * dw).sum())) < 1e-7 * max(1.0, abs(fd))
+    np.testing.assert_allclose(gb, R.reshape(-1, 3).sum(axis=0))
+
+
+def test_network_gradients_match_finite_differences():
+    g = np.random.default_rng(11)
+    chans = [3, 4, 4, 4, 1]
+    params = [(0.3 * g.standard_normal((27, chans[i], chans[i + 1])), 0.1 * g.standard_normal(chans[i + 1]))
+              for i in range(4)]
+    x = g.standard_normal((5, 4, 6, 3))
+    target = g.standard_normal((5, 4, 6, 1))
+
+    def loss(ps):
+        acts, _ = cnn.network_forward(x, ps)
+        return 0.5 * float(((acts[-1] - target) ** 2).sum())
+
+    acts, pre = cnn.network_forward(x, params)
+    grads = cnn.network_backward(acts, pre, params, acts[-1] - target)
+    eps = 1e-6
+    for li in range(4):
+        dw = g.standard_normal(params[li][0].shape)
+        pp = [p for p in params]
+        pp[li] = (params[li][0] + eps * dw, params[li][1])
+        pm = [p for p in params]
+        pm[li] = (params[li][0] - eps * dw, params[li][1])
+        fd = (loss(pp) - loss(pm)) / (2 * eps)
+        an = float((grads[li][0] * dw).sum())
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (li, fd, an)
+
+
+def test_bf16_round():
+    vals = np.array([1.0, 1.00390625, 1.005859375, 1.0078125, -3.1415926, 1e-30, 65504.0], dtype=np.float32)
+    r = cnn.bf16_round(vals)
+    assert r[0] == 1.0
+    assert r[1] == 1.0  # exactly halfway to 1.0078125: ties to even keeps 1.0
+    assert r[2] == np.float32(1.0078125)
+    assert r[3] == np.float32(1.0078125)
+    assert abs(r[4] - vals[4]) <= 2 ** -8 * abs(vals[4])
+    # every result is representable in 8 significand bits
+    assert np.all((r.view(np.uint32) & 0xFFFF) == 0)
