@@ -338,6 +338,54 @@ fd_status fd_batch_info(const fd_batch *batch, int *rows, int *stages, int *ctas
 void fd_batch_destroy(fd_batch *batch);
 
 /* ------------------------------------------------------------------------
+ * Learned closure: the 3x3x3 CNN that corrects a coarse-grid update
+ * ------------------------------------------------------------------------ */
+
+/* These calls have no counterpart in the paper: they implement a small 3D CNN
+ * whose output is added to each update of a coarse-grid acoustic operator (a
+ * learned closure of its discretisation error), trained on wavefields of the
+ * fine-grid operator.  Activations are device BF16, channels-last with 16
+ * channels per point (32 bytes), dense over a 3D shape (n0, n1, n2) with no
+ * padding; smaller channel counts are zero-padded.  A layer is
+ *   y[p][o] = b[o] + sum_{taps t} sum_c w[t][c][o] x[p + offset_t][c]
+ * (3x3x3 cross-correlation, zero outside the grid; tap t = (a+1)*9 + (b+1)*3
+ * + (c+1) for offsets a, b, c in {-1, 0, 1}), BF16 operands on the tensor
+ * cores with FP32 accumulation.  All calls enqueue on cuda_stream. */
+
+/* Pack FP32 device weights w[27][cin][cout] (cin, cout <= 16) into the
+ * tensor-core operand layout frag (27 * ceil(n/8) * 256 bytes, n = cout, or
+ * cin when flip = 1).  flip = 1 packs the input-gradient convolution: taps
+ * mirrored and channel axes exchanged, so that fd_cnn_conv3d with it maps
+ * dL/dy (cout channels) to dL/dx (cin channels). */
+fd_status fd_cnn_pack_weights(const float *w, int cin, int cout, int flip, void *frag, void *cuda_stream);
+/* One layer: y = relu?(conv(x, frag) + bias) [* (mask > 0)]; bias (FP32,
+ * cout) may be NULL; mask (BF16 activations) may be NULL.  y_fp32 = 1 writes
+ * a single linear channel as FP32 [n0*n1*n2] (cout must be 1), else BF16
+ * activations.  shape: 3 int64. */
+fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const void *frag, const float *bias, int cout,
+                        int relu, const void *mask, void *y, int y_fp32, void *cuda_stream);
+/* Weight and bias gradients of a layer, accumulated (+=) into FP32
+ * gw[27][cin][cout] and gb[cout]: gw[t][c][o] += sum_p x[p + offset_t][c]
+ * gy[p][o]. */
+fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, const void *gy, int cin, int cout, float *gw,
+                              float *gb, void *cuda_stream);
+/* Closure inputs from a grid's fields (fd_field_layout slots): channel 0 =
+ * u/scale, 1 = (u - u_prev)/scale, 2 = (1/sqrt(m) - v0)/v1, others 0. */
+fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m, double scale,
+                          double v0, double v1, void *x, void *cuda_stream);
+/* u += scale * corr at every interior node (corr: FP32 [n0*n1*n2]). */
+fd_status fd_cnn_add_correction(const fd_grid *grid, float *u, const float *corr, double scale, void *cuda_stream);
+/* Mean-squared error of pred against target/scale (target: a grid slot):
+ * *loss += mean (pred - target/scale)^2 (FP32, device), and its gradient
+ * 2 (pred - target/scale) / count into gy (BF16 activations, channel 0). */
+fd_status fd_cnn_mse_grad(const fd_grid *grid, const float *pred, const float *target, double scale, void *gy,
+                          float *loss, void *cuda_stream);
+/* One Adam step (Kingma and Ba 2015) on n FP32 parameters with moments m1, m2
+ * (step >= 1 counts from 1). */
+fd_status fd_cnn_adam(float *params, const float *grads, float *m1, float *m2, int64_t n, double lr, double beta1,
+                      double beta2, double eps, int64_t step, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Interpolation without allocation (the paper has no counterpart)
  * ------------------------------------------------------------------------ */
 

@@ -89,6 +89,16 @@ _SIGNATURES = [
     ("fd_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), _c_i64p]),
     ("fd_batch_destroy", None, [_vp]),
+    ("fd_cnn_pack_weights", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    ("fd_cnn_conv3d", ctypes.c_int, [_c_i64p, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
+                                     _vp]),
+    ("fd_cnn_conv3d_wgrad", ctypes.c_int, [_c_i64p, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    ("fd_cnn_features", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       _vp, _vp]),
+    ("fd_cnn_add_correction", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
+    ("fd_cnn_mse_grad", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    ("fd_cnn_adam", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int64, _vp]),
     ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -320,6 +330,45 @@ def fd_batch_info(b):
 
 def fd_batch_destroy(b):
     lib().fd_batch_destroy(b)
+
+
+def _ptr(t):
+    return None if t is None else (t if isinstance(t, int) else t.data_ptr())
+
+
+def fd_cnn_pack_weights(w, cin, cout, flip, frag, stream=0):
+    _check(lib().fd_cnn_pack_weights(_ptr(w), int(cin), int(cout), int(flip), _ptr(frag), int(stream) or None))
+
+
+def fd_cnn_conv3d(shape, x, frag, bias, cout, relu, mask, y, y_fp32, stream=0):
+    shp = _i64(shape)
+    _check(lib().fd_cnn_conv3d(shp.ctypes.data_as(_c_i64p), _ptr(x), _ptr(frag), _ptr(bias), int(cout), int(relu),
+                               _ptr(mask), _ptr(y), int(y_fp32), int(stream) or None))
+
+
+def fd_cnn_conv3d_wgrad(shape, x, gy, cin, cout, gw, gb, stream=0):
+    shp = _i64(shape)
+    _check(lib().fd_cnn_conv3d_wgrad(shp.ctypes.data_as(_c_i64p), _ptr(x), _ptr(gy), int(cin), int(cout), _ptr(gw),
+                                     _ptr(gb), int(stream) or None))
+
+
+def fd_cnn_features(grid, u, u_prev, m, scale, v0, v1, x, stream=0):
+    _check(lib().fd_cnn_features(grid, _ptr(u), _ptr(u_prev), _ptr(m), float(scale), float(v0), float(v1), _ptr(x),
+                                 int(stream) or None))
+
+
+def fd_cnn_add_correction(grid, u, corr, scale, stream=0):
+    _check(lib().fd_cnn_add_correction(grid, _ptr(u), _ptr(corr), float(scale), int(stream) or None))
+
+
+def fd_cnn_mse_grad(grid, pred, target, scale, gy, loss, stream=0):
+    _check(lib().fd_cnn_mse_grad(grid, _ptr(pred), _ptr(target), float(scale), _ptr(gy), _ptr(loss),
+                                 int(stream) or None))
+
+
+def fd_cnn_adam(params, grads, m1, m2, n, lr, beta1, beta2, eps, step, stream=0):
+    _check(lib().fd_cnn_adam(_ptr(params), _ptr(grads), _ptr(m1), _ptr(m2), int(n), float(lr), float(beta1),
+                             float(beta2), float(eps), int(step), int(stream) or None))
 
 
 def fd_interpolate_noalloc(grid, coords, dev_field, dev_out, stream=0):
