@@ -14,7 +14,9 @@ Conventions (channels-last, as the device stores activations):
   3x3x3 cross-correlation.
 
 The network: conv(C0 -> 16) ReLU, conv(16 -> 16) ReLU, conv(16 -> 16) ReLU,
-conv(16 -> 1); the closure adds its output to the coarse update.
+conv(16 -> 1), no biases; the closure adds rho times its output to the coarse
+update.  Also here: the closure's input features, the fine-to-coarse
+injection, the training loss and Adam (Kingma and Ba 2015, Algorithm 1).
 """
 import numpy as np
 
@@ -66,7 +68,8 @@ def conv3d_grad_weight(x, gy):
 
 
 def network_forward(x, params):
-    """Activations of the 4-layer network; params = [(w, b)] * 4."""
+    """Activations of the 4-layer network; params = [(w, b)] * 4 (b may be
+    zeros: the closure's network has none)."""
     acts = [np.asarray(x, dtype=np.float64)]
     pre = []
     h = acts[0]
@@ -98,3 +101,39 @@ def bf16_round(a):
     lsb = (u >> 16) & 1
     r = ((u + 0x7FFF + lsb) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).reshape(a.shape)
+
+
+def features(u, u_prev, m, scale, vref):
+    """Closure inputs [n0, n1, n2, 6]: with du = u - u_prev and
+    q = 1/(m vref^2), (u, du, q u, q du, q^2 u, q^2 du) / scale."""
+    u = np.asarray(u, dtype=np.float64)
+    du = u - np.asarray(u_prev, dtype=np.float64)
+    q = 1.0 / (np.asarray(m, dtype=np.float64) * vref * vref)
+    return np.stack([u, du, q * u, q * du, q * q * u, q * q * du], axis=-1) / scale
+
+
+def restrict(fine, factor):
+    """Coarse field whose node i is fine node factor*i on every axis."""
+    return np.asarray(fine)[::factor, ::factor, ::factor]
+
+
+def mse_and_grad(pred, residual):
+    """(mean (pred - residual)^2, its gradient with respect to pred)."""
+    e = np.asarray(pred, dtype=np.float64) - np.asarray(residual, dtype=np.float64)
+    return float((e * e).mean()), 2.0 * e / e.size
+
+
+def adam(params, grads, m1, m2, lr, beta1, beta2, eps, step):
+    """One Adam update (step counts from 1); returns new (params, m1, m2)."""
+    m1 = beta1 * m1 + (1.0 - beta1) * grads
+    m2 = beta2 * m2 + (1.0 - beta2) * grads * grads
+    mhat = m1 / (1.0 - beta1 ** step)
+    vhat = m2 / (1.0 - beta2 ** step)
+    return params - lr * mhat / (np.sqrt(vhat) + eps), m1, m2
+
+
+def closure_correction(u, u_prev, m, params, rho, vref):
+    """rho * network(features(u^n, u^{n-1})): the term the learned closure
+    adds to the coarse update (scale 1: the network is homogeneous)."""
+    acts, _ = network_forward(features(u, u_prev, m, 1.0, vref), params)
+    return rho * acts[-1][..., 0]

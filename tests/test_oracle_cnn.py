@@ -5,7 +5,12 @@
   * input and weight gradients of conv3d equal central finite differences of
     a random linear functional (FP64);
   * the whole network's parameter gradients equal finite differences;
-  * bf16_round matches the round-to-nearest-even definition on edge cases.
+  * bf16_round matches the round-to-nearest-even definition on edge cases;
+  * the closure features are linear in the wavefield and equal (u, du, u, du,
+    u, du) where the velocity is vref; the restriction keeps coinciding
+    nodes; the first Adam step moves every parameter by lr sign(g); the MSE
+    gradient matches finite differences; a bias-free ReLU network is
+    positively homogeneous (the property the closure relies on).
 """
 import itertools
 
@@ -101,3 +106,50 @@ def test_bf16_round():
     assert abs(r[4] - vals[4]) <= 2 ** -8 * abs(vals[4])
     # every result is representable in 8 significand bits
     assert np.all((r.view(np.uint32) & 0xFFFF) == 0)
+
+
+def test_features_linear_and_reference_velocity():
+    g = np.random.default_rng(12)
+    u, up = g.standard_normal((3, 4, 5)), g.standard_normal((3, 4, 5))
+    vref = 3000.0
+    m = np.full((3, 4, 5), 1.0 / vref ** 2)
+    f = cnn.features(u, up, m, 2.0, vref)
+    for c in range(3):
+        np.testing.assert_allclose(f[..., 2 * c], u / 2.0, rtol=1e-14)
+        np.testing.assert_allclose(f[..., 2 * c + 1], (u - up) / 2.0, rtol=1e-14, atol=1e-15)
+    m2 = np.full((3, 4, 5), 1.0 / (2 * vref) ** 2)  # twice the velocity: q = 4
+    f2 = cnn.features(3 * u, 3 * up, m2, 1.0, vref)
+    np.testing.assert_allclose(f2[..., 4], 48.0 * u, rtol=1e-13)
+
+
+def test_restrict_keeps_coinciding_nodes():
+    fine = np.arange(9 * 7 * 5, dtype=np.float64).reshape(9, 7, 5)
+    c = cnn.restrict(fine, 2)
+    assert c.shape == (5, 4, 3)
+    assert c[2, 3, 1] == fine[4, 6, 2]
+
+
+def test_adam_first_step_and_mse_gradient():
+    g = np.random.default_rng(13)
+    p = g.standard_normal(50)
+    gr = g.standard_normal(50)
+    p1, m1, m2 = cnn.adam(p, gr, np.zeros(50), np.zeros(50), 1e-2, 0.9, 0.999, 0.0, 1)
+    np.testing.assert_allclose(p1, p - 1e-2 * np.sign(gr), rtol=1e-12)
+    pred, res = g.standard_normal(20), g.standard_normal(20)
+    loss, gp = cnn.mse_and_grad(pred, res)
+    d = g.standard_normal(20)
+    eps = 1e-6
+    fd = (cnn.mse_and_grad(pred + eps * d, res)[0] - cnn.mse_and_grad(pred - eps * d, res)[0]) / (2 * eps)
+    assert abs(fd - float(gp @ d)) < 1e-8
+
+
+def test_bias_free_network_is_homogeneous():
+    g = np.random.default_rng(14)
+    chans = [6, 5, 5, 5, 1]
+    params = [(g.standard_normal((27, chans[i], chans[i + 1])), np.zeros(chans[i + 1])) for i in range(4)]
+    u, up = g.standard_normal((4, 5, 6)), g.standard_normal((4, 5, 6))
+    m = np.full((4, 5, 6), 1.0 / 2500.0 ** 2)
+    a = cnn.closure_correction(u, up, m, params, 0.5, 3000.0)
+    b = cnn.closure_correction(7.5 * u, 7.5 * up, m, params, 0.5, 3000.0)
+    np.testing.assert_allclose(b, 7.5 * a, rtol=1e-12, atol=1e-14)
+    assert np.all(cnn.closure_correction(0 * u, 0 * up, m, params, 0.5, 3000.0) == 0.0)
