@@ -369,17 +369,28 @@ fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const void *frag, c
  * gy[p][o]. */
 fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, const void *gy, int cin, int cout, float *gw,
                               float *gb, void *cuda_stream);
-/* Closure inputs from a grid's fields (fd_field_layout slots): channel 0 =
- * u/scale, 1 = (u - u_prev)/scale, 2 = (1/sqrt(m) - v0)/v1, others 0. */
+/* Closure inputs from a grid's fields (device FP32 slots of `grid`'s
+ * fd_field_layout): with du = u - u_prev and q = 1/(m vref^2), channels 0..5
+ * of x = (u, du, q u, q du, q^2 u, q^2 du) / scale, channels 6..15 = 0 (every
+ * channel linear in the wavefield, so that a network without biases is
+ * positively homogeneous in it).  x: BF16 activations of grid's shape. */
 fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m, double scale,
-                          double v0, double v1, void *x, void *cuda_stream);
+                          double vref, void *x, void *cuda_stream);
+/* Injection of a fine-grid field into a coarse grid whose nodes are every
+ * factor-th fine node: coarse[i, j, k] = fine[f i, f j, f k]; the fine shape
+ * must be factor * (n - 1) + 1 per axis (FD_ERR_INVALID_ARG otherwise).  Both
+ * are device FP32 slots of their grid's layout.  sumsq (device FP32, may be
+ * NULL): += the sum of the squared coarse values. */
+fd_status fd_cnn_restrict(const fd_grid *fine_grid, const float *fine, const fd_grid *coarse_grid, float *coarse,
+                          int factor, float *sumsq, void *cuda_stream);
 /* u += scale * corr at every interior node (corr: FP32 [n0*n1*n2]). */
 fd_status fd_cnn_add_correction(const fd_grid *grid, float *u, const float *corr, double scale, void *cuda_stream);
-/* Mean-squared error of pred against target/scale (target: a grid slot):
- * *loss += mean (pred - target/scale)^2 (FP32, device), and its gradient
- * 2 (pred - target/scale) / count into gy (BF16 activations, channel 0). */
-fd_status fd_cnn_mse_grad(const fd_grid *grid, const float *pred, const float *target, double scale, void *gy,
-                          float *loss, void *cuda_stream);
+/* Mean-squared error of pred against r = (target - base)/scale (target, base:
+ * grid slots; base may be NULL for 0): *loss += mean (pred - r)^2 (FP32,
+ * device), and its gradient 2 (pred - r) / count into gy (BF16 activations,
+ * channel 0, the other channels zero). */
+fd_status fd_cnn_mse_grad(const fd_grid *grid, const float *pred, const float *target, const float *base,
+                          double scale, void *gy, float *loss, void *cuda_stream);
 /* One Adam step (Kingma and Ba 2015) on n FP32 parameters with moments m1, m2
  * (step >= 1 counts from 1). */
 fd_status fd_cnn_adam(float *params, const float *grads, float *m1, float *m2, int64_t n, double lr, double beta1,

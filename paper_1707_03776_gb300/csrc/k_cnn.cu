@@ -177,6 +177,9 @@ __global__ void __launch_bounds__(32 * kT1)
                                 __floats2bfloat162_rn(v0, v1);
                         }
                     }
+                    if (!OUT_F32 && NT == 1)  // channels 8..15 of a narrow output are zero
+                        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(y) + pt * kC + 8 +
+                                                            tig * 2) = __floats2bfloat162_rn(0.f, 0.f);
                 }
             }
         }
@@ -264,10 +267,11 @@ __global__ void __launch_bounds__(256)
     if (c == 0) atomicAdd(&gb[o], accb);
 }
 
-// Closure input features: channel 0 = u^n / s, 1 = (u^n - u^{n-1}) / s,
-// 2 = velocity feature (v - v0) / v1 with v = 1/sqrt(m), 3..15 = 0.
+// Closure input features, all linear in the wavefield: with du = u^n -
+// u^{n-1} and q = 1/(m vref^2) (the squared velocity relative to vref),
+// channels 0..5 = (u, du, q u, q du, q^2 u, q^2 du) / s; 6..15 = 0.
 __global__ void features_kernel(Geom g, const float *__restrict__ u, const float *__restrict__ up,
-                                const float *__restrict__ m, float inv_scale, float v0, float inv_v1,
+                                const float *__restrict__ m, float inv_scale, float inv_vref2,
                                 __nv_bfloat16 *__restrict__ x)
 {
     const long long total = g.n[0] * g.n[1] * g.n[2];
@@ -277,12 +281,36 @@ __global__ void features_kernel(Geom g, const float *__restrict__ u, const float
         const long long i2 = p - row * g.n[2];
         const long long i0 = row / g.n[1], i1 = row - i0 * g.n[1];
         const long long at = i0 * g.s0 + i1 * g.s1 + i2;
-        const float a = u[at], b = up[at];
-        const float v = rsqrtf(m[at]);
+        const float a = u[at] * inv_scale, b = (u[at] - up[at]) * inv_scale;
+        const float q = inv_vref2 / m[at];
         __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(x + p * kC);
-        dst[0] = __floats2bfloat162_rn(a * inv_scale, (a - b) * inv_scale);
-        dst[1] = __floats2bfloat162_rn((v - v0) * inv_v1, 0.f);
-        for (int k = 2; k < kC / 2; k++) dst[k] = __floats2bfloat162_rn(0.f, 0.f);
+        dst[0] = __floats2bfloat162_rn(a, b);
+        dst[1] = __floats2bfloat162_rn(q * a, q * b);
+        dst[2] = __floats2bfloat162_rn(q * q * a, q * q * b);
+        for (int k = 3; k < kC / 2; k++) dst[k] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+}
+
+// coarse[i] = fine[f i] per axis (injection of a fine grid whose nodes
+// include every coarse node: n_fine = f (n_coarse - 1) + 1); optionally
+// *sumsq += sum of the squared coarse values.
+__global__ void restrict_kernel(Geom gc, Geom gf, int f, const float *__restrict__ fine, float *__restrict__ coarse,
+                                float *sumsq)
+{
+    const long long total = gc.n[0] * gc.n[1] * gc.n[2];
+    float local = 0.f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long row = p / gc.n[2];
+        const long long i2 = p - row * gc.n[2];
+        const long long i0 = row / gc.n[1], i1 = row - i0 * gc.n[1];
+        const float v = fine[f * (i0 * gf.s0 + i1 * gf.s1 + i2)];
+        coarse[i0 * gc.s0 + i1 * gc.s1 + i2] = v;
+        local += v * v;
+    }
+    if (sumsq) {
+        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(sumsq, local);
     }
 }
 
@@ -299,12 +327,12 @@ __global__ void add_correction_kernel(Geom g, float *__restrict__ u, const float
     }
 }
 
-// MSE loss of pred against target / s and its gradient into gy (BF16,
-// channel 0; other channels zero): loss += sum (pred - t/s)^2 / count,
-// gy = 2 (pred - t/s) / count.
+// MSE loss of pred against r = (target - base) / s (base may be NULL) and its
+// gradient into gy (BF16, channel 0; other channels zero):
+// loss += sum (pred - r)^2 / count, gy = 2 (pred - r) / count.
 __global__ void mse_grad_kernel(long long count, const float *__restrict__ pred, Geom g,
-                                const float *__restrict__ target, float inv_scale, __nv_bfloat16 *__restrict__ gy,
-                                float *loss)
+                                const float *__restrict__ target, const float *__restrict__ base, float inv_scale,
+                                __nv_bfloat16 *__restrict__ gy, float *loss)
 {
     float local = 0.f;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
@@ -312,7 +340,9 @@ __global__ void mse_grad_kernel(long long count, const float *__restrict__ pred,
         const long long row = p / g.n[2];
         const long long i2 = p - row * g.n[2];
         const long long i0 = row / g.n[1], i1 = row - i0 * g.n[1];
-        const float e = pred[p] - target[i0 * g.s0 + i1 * g.s1 + i2] * inv_scale;
+        const long long at = i0 * g.s0 + i1 * g.s1 + i2;
+        const float r = (base ? target[at] - base[at] : target[at]) * inv_scale;
+        const float e = pred[p] - r;
         local += e * e;
         __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(gy + p * kC);
         dst[0] = __floats2bfloat162_rn(2.f * e / (float)count, 0.f);
@@ -371,6 +401,19 @@ static fd_status cnn_dims(int ndim, const int64_t *shape, CnnDims *d)
     d->n1 = (int)shape[1];
     d->n2 = (int)shape[2];
     return FD_OK;
+}
+
+static Geom geom3(const fd_grid *grid)
+{
+    Geom g;
+    g.ndim = 3;
+    const int64_t S = (grid->shape[2] + 7) / 8 * 8;
+    g.n[0] = grid->shape[0];
+    g.n[1] = grid->shape[1];
+    g.n[2] = grid->shape[2];
+    g.s0 = grid->shape[1] * S;
+    g.s1 = S;
+    return g;
 }
 
 #define CNN_CUDA(call, what)                                                                           \
@@ -437,22 +480,31 @@ extern "C" fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, co
 }
 
 extern "C" fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m,
-                                     double scale, double v0, double v1, void *x, void *stream)
+                                     double scale, double vref, void *x, void *stream)
 {
-    if (!grid || grid->ndim != 3 || !u || !u_prev || !m || !x || !(scale > 0) || !(v1 > 0))
+    if (!grid || grid->ndim != 3 || !u || !u_prev || !m || !x || !(scale > 0) || !(vref > 0))
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_features: bad arguments");
-    Geom g;
-    g.ndim = 3;
-    const int64_t S = (grid->shape[2] + 7) / 8 * 8;
-    g.n[0] = grid->shape[0];
-    g.n[1] = grid->shape[1];
-    g.n[2] = grid->shape[2];
-    g.s0 = grid->shape[1] * S;
-    g.s1 = S;
+    const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     features_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-        g, u, u_prev, m, (float)(1.0 / scale), (float)v0, (float)(1.0 / v1), (__nv_bfloat16 *)x);
+        g, u, u_prev, m, (float)(1.0 / scale), (float)(1.0 / (vref * vref)), (__nv_bfloat16 *)x);
     CNN_CUDA(cudaGetLastError(), "fd_cnn_features");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_cnn_restrict(const fd_grid *fine_grid, const float *fine, const fd_grid *coarse_grid,
+                                     float *coarse, int factor, float *sumsq, void *stream)
+{
+    if (!fine_grid || !coarse_grid || fine_grid->ndim != 3 || coarse_grid->ndim != 3 || !fine || !coarse ||
+        factor < 1)
+        return set_error(FD_ERR_INVALID_ARG, "fd_cnn_restrict: bad arguments");
+    for (int a = 0; a < 3; a++)
+        if (fine_grid->shape[a] != factor * (coarse_grid->shape[a] - 1) + 1)
+            return set_error(FD_ERR_INVALID_ARG, "fd_cnn_restrict: fine shape must be factor*(n-1)+1 per axis");
+    const Geom gc = geom3(coarse_grid), gf = geom3(fine_grid);
+    const long long total = gc.n[0] * gc.n[1] * gc.n[2];
+    restrict_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(gc, gf, factor, fine, coarse, sumsq);
+    CNN_CUDA(cudaGetLastError(), "fd_cnn_restrict");
     return FD_OK;
 }
 
@@ -460,36 +512,22 @@ extern "C" fd_status fd_cnn_add_correction(const fd_grid *grid, float *u, const 
                                            void *stream)
 {
     if (!grid || grid->ndim != 3 || !u || !corr) return set_error(FD_ERR_INVALID_ARG, "fd_cnn_add_correction: bad arguments");
-    Geom g;
-    g.ndim = 3;
-    const int64_t S = (grid->shape[2] + 7) / 8 * 8;
-    g.n[0] = grid->shape[0];
-    g.n[1] = grid->shape[1];
-    g.n[2] = grid->shape[2];
-    g.s0 = grid->shape[1] * S;
-    g.s1 = S;
+    const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     add_correction_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(g, u, corr, (float)scale);
     CNN_CUDA(cudaGetLastError(), "fd_cnn_add_correction");
     return FD_OK;
 }
 
-extern "C" fd_status fd_cnn_mse_grad(const fd_grid *grid, const float *pred, const float *target, double scale,
-                                     void *gy, float *loss, void *stream)
+extern "C" fd_status fd_cnn_mse_grad(const fd_grid *grid, const float *pred, const float *target, const float *base,
+                                     double scale, void *gy, float *loss, void *stream)
 {
     if (!grid || grid->ndim != 3 || !pred || !target || !gy || !loss || !(scale > 0))
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_mse_grad: bad arguments");
-    Geom g;
-    g.ndim = 3;
-    const int64_t S = (grid->shape[2] + 7) / 8 * 8;
-    g.n[0] = grid->shape[0];
-    g.n[1] = grid->shape[1];
-    g.n[2] = grid->shape[2];
-    g.s0 = grid->shape[1] * S;
-    g.s1 = S;
+    const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     mse_grad_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-        total, pred, g, target, (float)(1.0 / scale), (__nv_bfloat16 *)gy, loss);
+        total, pred, g, target, base, (float)(1.0 / scale), (__nv_bfloat16 *)gy, loss);
     CNN_CUDA(cudaGetLastError(), "fd_cnn_mse_grad");
     return FD_OK;
 }

@@ -93,10 +93,10 @@ _SIGNATURES = [
     ("fd_cnn_conv3d", ctypes.c_int, [_c_i64p, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
                                      _vp]),
     ("fd_cnn_conv3d_wgrad", ctypes.c_int, [_c_i64p, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
-    ("fd_cnn_features", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                       _vp, _vp]),
+    ("fd_cnn_features", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    ("fd_cnn_restrict", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
     ("fd_cnn_add_correction", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
-    ("fd_cnn_mse_grad", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    ("fd_cnn_mse_grad", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     ("fd_cnn_adam", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64, _vp]),
     ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -352,8 +352,13 @@ def fd_cnn_conv3d_wgrad(shape, x, gy, cin, cout, gw, gb, stream=0):
                                      _ptr(gb), int(stream) or None))
 
 
-def fd_cnn_features(grid, u, u_prev, m, scale, v0, v1, x, stream=0):
-    _check(lib().fd_cnn_features(grid, _ptr(u), _ptr(u_prev), _ptr(m), float(scale), float(v0), float(v1), _ptr(x),
+def fd_cnn_features(grid, u, u_prev, m, scale, vref, x, stream=0):
+    _check(lib().fd_cnn_features(grid, _ptr(u), _ptr(u_prev), _ptr(m), float(scale), float(vref), _ptr(x),
+                                 int(stream) or None))
+
+
+def fd_cnn_restrict(fine_grid, fine, coarse_grid, coarse, factor, sumsq=None, stream=0):
+    _check(lib().fd_cnn_restrict(fine_grid, _ptr(fine), coarse_grid, _ptr(coarse), int(factor), _ptr(sumsq),
                                  int(stream) or None))
 
 
@@ -361,8 +366,8 @@ def fd_cnn_add_correction(grid, u, corr, scale, stream=0):
     _check(lib().fd_cnn_add_correction(grid, _ptr(u), _ptr(corr), float(scale), int(stream) or None))
 
 
-def fd_cnn_mse_grad(grid, pred, target, scale, gy, loss, stream=0):
-    _check(lib().fd_cnn_mse_grad(grid, _ptr(pred), _ptr(target), float(scale), _ptr(gy), _ptr(loss),
+def fd_cnn_mse_grad(grid, pred, target, base, scale, gy, loss, stream=0):
+    _check(lib().fd_cnn_mse_grad(grid, _ptr(pred), _ptr(target), _ptr(base), float(scale), _ptr(gy), _ptr(loss),
                                  int(stream) or None))
 
 

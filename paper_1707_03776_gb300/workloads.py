@@ -251,3 +251,88 @@ def window_shot(cfg, i):
     X, Y = np.meshgrid(gx, gy, indexing="ij")
     rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, depth + 0.5)], axis=1) * h
     return shape, m, eta, src, rec
+
+
+def layered_velocity(shape, spacing, seed, vmin=1500.0, vmax=3500.0, extent=None):
+    """Seeded random layered model (FP64 velocity on the grid's nodes): 3 to 6
+    layers below the surface whose interfaces are planes
+    z = z_k + s_k x + t_k y with dips of at most ~6 degrees, velocities drawn
+    uniform in [vmin, vmax] and sorted to increase with depth.  The model is a
+    function of physical position (origin 0, `extent` metres per axis, by
+    default the grid's), so grids of different spacing over one extent sample
+    the same model."""
+    g = np.random.default_rng(SEED_BASE + 7919 * seed)
+    ext = [(n - 1) * h for n, h in zip(shape, spacing)] if extent is None else list(extent)
+    nl = int(g.integers(3, 7))
+    vel = np.sort(g.uniform(vmin, vmax, nl))
+    z0 = np.sort(g.uniform(0.15, 0.9, nl - 1)) * ext[2]
+    sx = g.uniform(-0.1, 0.1, nl - 1)
+    sy = g.uniform(-0.1, 0.1, nl - 1)
+    x = np.arange(shape[0]) * spacing[0] - 0.5 * ext[0]
+    y = np.arange(shape[1]) * spacing[1] - 0.5 * ext[1]
+    z = np.arange(shape[2]) * spacing[2]
+    X, Y, Z = np.meshgrid(x, y, z, indexing="ij", sparse=True)
+    layer = np.zeros(np.broadcast_shapes(X.shape, Y.shape, Z.shape), dtype=np.int64)
+    for k in range(nl - 1):
+        layer += (Z >= z0[k] + sx[k] * X + sy[k] * Y).astype(np.int64)
+    return vel[layer]
+
+
+def closure_config(n_coarse=48, nt=400, seed=0, sponge=8, f0=8.0, vmin=1500.0, vmax=3500.0, cfl=0.3,
+                   src="random", nrec_side=None):
+    """One learned-closure experiment: the same layered model, source and
+    receivers on a coarse grid (n_coarse^3 nodes at 20 m, SO4) and on the fine
+    grid whose every other node is a coarse node ((2 n_coarse - 1)^3 at 10 m,
+    SO16).  dt_fine = cfl * 10 m / vmax and dt_coarse = 2 dt_fine (the same
+    Courant number on both grids); the fine run takes 2 nt steps.
+
+    The source sits on a coarse node: a random interior node (src="random") or
+    the centre of the top face just below the sponge (src="surface").  The
+    Ricker amplitude is divided by each grid's cell volume (the injection adds
+    amplitude * dt^2/m at the nodes, so this discretises one point source of
+    unit strength on both grids).  Receivers: a square lattice of coarse nodes
+    (every other one) on the plane one coarse cell below the source depth of
+    a surface source.  Sponges of `sponge` coarse cells (twice as many fine
+    cells) with sigma_max of a 20-coarse-cell layer: the same physical
+    profile on both grids."""
+    g = np.random.default_rng(SEED_BASE + 104729 * seed + 1)
+    hc, hf = 20.0, 10.0
+    nc = int(n_coarse)
+    nf = 2 * nc - 1
+    shape_c, shape_f = (nc,) * 3, (nf,) * 3
+    sp_c, sp_f = (hc,) * 3, (hf,) * 3
+    ext = [(nc - 1) * hc] * 3
+    v_c = layered_velocity(shape_c, sp_c, seed, vmin, vmax, ext)
+    v_f = layered_velocity(shape_f, sp_f, seed, vmin, vmax, ext)
+    dt_f = cfl * hf / vmax
+    dt_c = 2.0 * dt_f
+
+    def fields(v, shape, spacing, width):
+        m = (1.0 / v ** 2).astype(np.float32)
+        # sigma_max of a 400 m layer on both grids (20 coarse, 40 fine cells)
+        sigma = sponge_sigma(shape, spacing, width, vmax, ref_width=20 * width // sponge)
+        return m, (m.astype(np.float64) * sigma).astype(np.float32)
+
+    m_c, eta_c = fields(v_c, shape_c, sp_c, sponge)
+    m_f, eta_f = fields(v_f, shape_f, sp_f, 2 * sponge)
+    lo, hi = sponge + 4, nc - 1 - sponge - 4
+    if src == "random":
+        s_idx = g.integers(lo, hi + 1, size=3).astype(np.float64)
+    else:
+        s_idx = np.array([(nc - 1) // 2, (nc - 1) // 2, sponge + 2], dtype=np.float64)
+    src_coords = (s_idx * hc).reshape(1, 3)
+    side = np.arange(sponge + 1, nc - sponge - 1, 2, dtype=np.float64)
+    if nrec_side is not None:
+        side = side[:: max(1, side.size // int(nrec_side))][: int(nrec_side)]
+    X, Y = np.meshgrid(side, side, indexing="ij")
+    depth = float(sponge + 3)
+    rec_coords = np.stack([X.ravel(), Y.ravel(), np.full(X.size, depth)], axis=1) * hc
+    w_c = ricker(nt, dt_c, f0) / hc ** 3
+    w_f = ricker(2 * nt, dt_f, f0) / hf ** 3
+    return dict(
+        coarse=dict(shape=shape_c, spacing=sp_c, space_order=4, dt=dt_c, nt=nt, m=m_c, eta=eta_c,
+                    src_trace=w_c.astype(np.float32).reshape(nt, 1)),
+        fine=dict(shape=shape_f, spacing=sp_f, space_order=16, dt=dt_f, nt=2 * nt, m=m_f, eta=eta_f,
+                  src_trace=w_f.astype(np.float32).reshape(2 * nt, 1)),
+        origin=(0.0, 0.0, 0.0), src_coords=src_coords, rec_coords=rec_coords, vmax=vmax, vmin=vmin, f0=f0,
+        sponge=sponge, seed=seed)

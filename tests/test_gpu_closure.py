@@ -1,0 +1,295 @@
+"""Learned closure on the GPU against the CPU oracle (oracle/cnn.py).
+
+Operands are BF16 on both sides (the oracle takes the BF16-rounded inputs and
+weights in FP64), so the convolution's only difference is the GPU's FP32
+accumulation over K = 27 taps x 16 channels: |gpu - ref| <= 2e-5 * A, with A
+the same sum taken over absolute values (K * 2^-24 ~ 2.6e-5 bounds the
+relative error of a K-term FP32 sum; the tensor cores' accumulation stays
+within it).  BF16 outputs add one rounding: 2^-8 |ref|.  The whole network
+rounds every activation to BF16 (2^-9 relative each), which the oracle does
+not: gradients agree to a relative L2 error of 2e-2.
+
+Shapes span several CTA tiles in every direction with ragged ends (tiles of
+16 planes x 8 rows x 64 points).
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (20, 19, 70)
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _fd():
+    from paper_1707_03776_gb300 import fd
+    return fd
+
+
+def _bf16_acts(x16):
+    """numpy [N..., 16] -> (device BF16 tensor [Npts, 16], the BF16 values in FP64)."""
+    torch = _torch()
+    xr = cnn.bf16_round(np.asarray(x16, dtype=np.float32))
+    t = torch.from_numpy(xr.reshape(-1, 16)).to(torch.bfloat16).cuda()
+    return t, xr.astype(np.float64)
+
+
+def _pad16(x):
+    out = np.zeros(x.shape[:3] + (16,), dtype=x.dtype)
+    out[..., : x.shape[3]] = x
+    return out
+
+
+def _pack(w, flip=0):
+    torch = _torch()
+    fd = _fd()
+    cin, cout = w.shape[1], w.shape[2]
+    n = cin if flip else cout
+    frag = torch.zeros(27 * ((n + 7) // 8) * 256, dtype=torch.uint8, device="cuda")
+    wd = torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).cuda()
+    fd.fd_cnn_pack_weights(wd, cin, cout, flip, frag, torch.cuda.current_stream().cuda_stream)
+    return frag, cnn.bf16_round(w.astype(np.float32)).astype(np.float64)
+
+
+@pytest.mark.parametrize("cin,cout,relu,mask", [(6, 16, True, False), (16, 16, False, True), (16, 5, True, True),
+                                                (3, 8, False, False)])
+def test_conv3d_parity(cin, cout, relu, mask):
+    torch = _torch()
+    fd = _fd()
+    g = np.random.default_rng(100 + cin + cout)
+    x = _pad16(g.standard_normal(SHAPE + (cin,)).astype(np.float32))
+    w = (g.standard_normal((27, cin, cout)) / np.sqrt(27 * cin)).astype(np.float32)
+    b = g.standard_normal(cout).astype(np.float32)
+    xt, xr = _bf16_acts(x)
+    frag, wr = _pack(w)
+    bt = torch.from_numpy(b).cuda()
+    mk = g.standard_normal(SHAPE + (16,)).astype(np.float32)
+    mt, mr = _bf16_acts(mk)
+    y = torch.full((xt.shape[0], 16), float("nan"), dtype=torch.bfloat16, device="cuda")
+    fd.fd_cnn_conv3d(SHAPE, xt, frag, bt, cout, int(relu), mt if mask else None, y, 0,
+                     torch.cuda.current_stream().cuda_stream)
+    got = y.float().cpu().numpy().reshape(SHAPE + (16,)).astype(np.float64)
+    ref = cnn.conv3d(xr[..., :cin], wr, b.astype(np.float64))
+    A = cnn.conv3d(np.abs(xr[..., :cin]), np.abs(wr), np.abs(b.astype(np.float64)))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    if mask:
+        ref = ref * (mr[..., :cout] > 0)
+    tol = 2.0 ** -8 * np.abs(ref) + 2e-5 * A
+    assert np.all(np.abs(got[..., :cout] - ref) <= tol + 1e-30)
+    assert np.all(got[..., cout:] == 0.0)  # channels beyond cout are written as zero
+
+
+def test_conv3d_fp32_output_parity():
+    torch = _torch()
+    fd = _fd()
+    g = np.random.default_rng(7)
+    x = g.standard_normal(SHAPE + (16,)).astype(np.float32)
+    w = (g.standard_normal((27, 16, 1)) / 20.0).astype(np.float32)
+    xt, xr = _bf16_acts(x)
+    frag, wr = _pack(w)
+    y = torch.zeros(xt.shape[0], dtype=torch.float32, device="cuda")
+    fd.fd_cnn_conv3d(SHAPE, xt, frag, None, 1, 0, None, y, 1, torch.cuda.current_stream().cuda_stream)
+    got = y.cpu().numpy().reshape(SHAPE).astype(np.float64)
+    ref = cnn.conv3d(xr, wr, np.zeros(1))[..., 0]
+    A = cnn.conv3d(np.abs(xr), np.abs(wr), np.zeros(1))[..., 0]
+    assert np.all(np.abs(got - ref) <= 2e-5 * A + 1e-30)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 1), (16, 16), (6, 16)])
+def test_conv3d_input_gradient_parity(cin, cout):
+    """The flipped pack turns the convolution into its input gradient."""
+    torch = _torch()
+    fd = _fd()
+    g = np.random.default_rng(200 + cin + cout)
+    gy = _pad16(g.standard_normal(SHAPE + (cout,)).astype(np.float32))
+    w = (g.standard_normal((27, cin, cout)) / np.sqrt(27 * cout)).astype(np.float32)
+    gt, gr = _bf16_acts(gy)
+    frag, wr = _pack(w, flip=1)
+    y = torch.zeros((gt.shape[0], 16), dtype=torch.bfloat16, device="cuda")
+    fd.fd_cnn_conv3d(SHAPE, gt, frag, None, cin, 0, None, y, 0, torch.cuda.current_stream().cuda_stream)
+    got = y.float().cpu().numpy().reshape(SHAPE + (16,)).astype(np.float64)
+    ref = cnn.conv3d_grad_input(gr[..., :cout], wr)
+    A = cnn.conv3d_grad_input(np.abs(gr[..., :cout]), np.abs(wr))
+    assert np.all(np.abs(got[..., :cin] - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-5 * A + 1e-30)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (6, 16), (16, 1)])
+def test_conv3d_weight_gradient_parity(cin, cout):
+    torch = _torch()
+    fd = _fd()
+    g = np.random.default_rng(300 + cin + cout)
+    x = _pad16(g.standard_normal(SHAPE + (cin,)).astype(np.float32))
+    gy = _pad16(g.standard_normal(SHAPE + (cout,)).astype(np.float32))
+    xt, xr = _bf16_acts(x)
+    gt, gr = _bf16_acts(gy)
+    gw = torch.full((27, cin, cout), 0.25, dtype=torch.float32, device="cuda")  # accumulates onto 0.25
+    gb = torch.zeros(16, dtype=torch.float32, device="cuda")
+    fd.fd_cnn_conv3d_wgrad(SHAPE, xt, gt, cin, cout, gw, gb, torch.cuda.current_stream().cuda_stream)
+    rw, rb = cnn.conv3d_grad_weight(xr[..., :cin], gr[..., :cout])
+    Aw, Ab = cnn.conv3d_grad_weight(np.abs(xr[..., :cin]), np.abs(gr[..., :cout]))
+    got = gw.cpu().numpy().astype(np.float64) - 0.25
+    assert np.all(np.abs(got - rw) <= 2e-5 * Aw + 1e-6)
+    assert np.all(np.abs(gb.cpu().numpy()[:cout] - rb) <= 2e-5 * Ab + 1e-6)
+
+
+def _grid_fields(shape, seed):
+    torch = _torch()
+    fd = _fd()
+    g = np.random.default_rng(seed)
+    grid = fd.Grid(shape, (20.0,) * 3)
+    u = fd.TimeData("u", grid)
+    m = fd.DenseData("m", grid)
+    un, up = g.standard_normal(shape).astype(np.float32), g.standard_normal(shape).astype(np.float32)
+    v = g.uniform(1500.0, 3500.0, shape)
+    mm = (1.0 / v ** 2).astype(np.float32)
+    u.view(0).copy_(torch.from_numpy(un))
+    u.view(1).copy_(torch.from_numpy(up))
+    m.data.copy_(torch.from_numpy(mm))
+    return grid, u, m, un, up, mm
+
+
+def test_features_restrict_correction_mse_adam():
+    torch = _torch()
+    fd = _fd()
+    st = torch.cuda.current_stream().cuda_stream
+    shape = (9, 10, 13)
+    grid, u, m, un, up, mm = _grid_fields(shape, 5)
+    n = int(np.prod(shape))
+    x = torch.full((n, 16), float("nan"), dtype=torch.bfloat16, device="cuda")
+    fd.fd_cnn_features(grid.handle, u.slots[0], u.slots[1], m.slots[0], 2.0, 3000.0, x, st)
+    ref = cnn.features(un, up, mm, 2.0, 3000.0)
+    got = x.float().cpu().numpy().reshape(shape + (16,))
+    assert np.all(np.abs(got[..., :6] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6 * np.abs(ref).max())
+    assert np.all(got[..., 6:] == 0.0)
+
+    # restriction from a (2n-1)-node fine grid, with the sum of squares
+    fshape = tuple(2 * s - 1 for s in shape)
+    fgrid = fd.Grid(fshape, (10.0,) * 3)
+    fu = fd.DenseData("f", fgrid)
+    fine = np.random.default_rng(6).standard_normal(fshape).astype(np.float32)
+    fu.data.copy_(torch.from_numpy(fine))
+    out = fd.DenseData("c", grid)
+    ss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    fd.fd_cnn_restrict(fgrid.handle, fu.slots[0], grid.handle, out.slots[0], 2, ss, st)
+    r = cnn.restrict(fine, 2)
+    assert np.array_equal(out.data.cpu().numpy(), r)
+    assert abs(float(ss.item()) - float((r.astype(np.float64) ** 2).sum())) <= 1e-5 * float((r ** 2).sum())
+    with pytest.raises(fd.FDError):
+        fd.fd_cnn_restrict(fgrid.handle, fu.slots[0], grid.handle, out.slots[0], 3, None, st)
+
+    # u += scale * corr
+    corr = np.random.default_rng(8).standard_normal(n).astype(np.float32)
+    fd.fd_cnn_add_correction(grid.handle, u.slots[0], torch.from_numpy(corr).cuda(), 0.5, st)
+    np.testing.assert_allclose(u.view(0).cpu().numpy(), un + np.float32(0.5) * corr.reshape(shape), rtol=1e-6,
+                               atol=1e-6)
+
+    # loss and gradient against (target - base)/s
+    pred = np.random.default_rng(9).standard_normal(n).astype(np.float32)
+    gy = torch.zeros((n, 16), dtype=torch.bfloat16, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    tgt, base = fd.DenseData("t", grid), fd.DenseData("b", grid)
+    tv = np.random.default_rng(10).standard_normal(shape).astype(np.float32)
+    bv = np.random.default_rng(11).standard_normal(shape).astype(np.float32)
+    tgt.data.copy_(torch.from_numpy(tv))
+    base.data.copy_(torch.from_numpy(bv))
+    fd.fd_cnn_mse_grad(grid.handle, torch.from_numpy(pred).cuda(), tgt.slots[0], base.slots[0], 4.0, gy, loss, st)
+    rl, rg = cnn.mse_and_grad(pred.reshape(shape), (tv.astype(np.float64) - bv) / 4.0)
+    assert abs(float(loss.item()) - rl) <= 1e-5 * rl
+    gg = gy.float().cpu().numpy().reshape(shape + (16,))
+    assert np.all(np.abs(gg[..., 0] - rg) <= 2.0 ** -8 * np.abs(rg) + 1e-12)
+    assert np.all(gg[..., 1:] == 0.0)
+
+    # Adam, three steps
+    g = np.random.default_rng(12)
+    p = g.standard_normal(1000)
+    pt = torch.from_numpy(p.astype(np.float32)).cuda()
+    m1 = torch.zeros_like(pt)
+    m2 = torch.zeros_like(pt)
+    rp, rm1, rm2 = p.astype(np.float32).astype(np.float64), np.zeros(1000), np.zeros(1000)
+    for step in (1, 2, 3):
+        gr = g.standard_normal(1000).astype(np.float32)
+        fd.fd_cnn_adam(pt, torch.from_numpy(gr).cuda(), m1, m2, 1000, 1e-3, 0.9, 0.999, 1e-8, step, st)
+        rp, rm1, rm2 = cnn.adam(rp, gr.astype(np.float64), rm1, rm2, 1e-3, 0.9, 0.999, 1e-8, step)
+    np.testing.assert_allclose(pt.cpu().numpy(), rp, rtol=0, atol=1e-6)
+
+
+def test_network_gradients_parity():
+    """Forward, loss and backward of the whole closure network (closure.py on
+    libfdgb) against the oracle's network on the same BF16 weights and
+    features."""
+    torch = _torch()
+    fd = _fd()
+    from paper_1707_03776_gb300 import closure
+    st = torch.cuda.current_stream().cuda_stream
+    shape = (18, 11, 67)
+    grid, u, m, un, up, mm = _grid_fields(shape, 21)
+    net = closure.ClosureNet(seed=3, rho=1.0)
+    ws = closure.Workspace(shape)
+    fd.fd_cnn_features(grid.handle, u.slots[0], u.slots[1], m.slots[0], 1.5, net.vref, ws.h[0], st)
+    closure.network_forward(net, ws, st)
+    tgt, base = fd.DenseData("t", grid), fd.DenseData("b", grid)
+    tv = np.random.default_rng(22).standard_normal(shape).astype(np.float32)
+    tgt.data.copy_(torch.from_numpy(tv))
+    net.grads.zero_()
+    fd.fd_cnn_mse_grad(grid.handle, ws.out, tgt.slots[0], None, 1.5, ws.g[0], ws.loss, st)
+    closure.network_backward(net, ws, st)
+
+    ws_np = [cnn.bf16_round(w).astype(np.float64) for w in net.weights()]
+    params = [(w, np.zeros(w.shape[2])) for w in ws_np]
+    x = cnn.bf16_round(cnn.features(un, up, mm, 1.5, net.vref).astype(np.float32)).astype(np.float64)
+    acts, pre = cnn.network_forward(x, params)
+    out_ref = acts[-1][..., 0]
+    out = ws.out.cpu().numpy().reshape(shape)
+    assert np.linalg.norm(out - out_ref) <= 2e-2 * np.linalg.norm(out_ref)
+    loss_ref, gout = cnn.mse_and_grad(out_ref, tv / 1.5)
+    assert abs(float(ws.loss.item()) - loss_ref) <= 2e-2 * loss_ref
+    grads = cnn.network_backward(acts, pre, params, gout[..., None])
+    for li in range(4):
+        got = net.grad(li).cpu().numpy()
+        ref = grads[li][0]
+        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref), li
+
+
+def test_closure_step_parity():
+    """One step of the closure operator = the oracle's coarse step from the
+    same state plus rho times the oracle network on the same weights."""
+    torch = _torch()
+    import oracle
+    from paper_1707_03776_gb300 import closure, workloads as wl
+    cfg = wl.closure_config(n_coarse=24, nt=40, seed=4, sponge=4)
+    c = cfg["coarse"]
+    net = closure.ClosureNet(seed=5, rho=0.01)
+    op = closure.ClosureOperator(cfg, net)
+    # 30 learned steps on the GPU, then the 31st step's pieces one by one
+    # from the GPU's state
+    op.run(30)
+    uc = op.u.view(30 % 2).cpu().numpy().copy()
+    upv = op.u.view(31 % 2).cpu().numpy().copy()
+    from paper_1707_03776_gb300 import fd
+    st = torch.cuda.current_stream().cuda_stream
+    fd.fd_cnn_features(op.grid.handle, op.u.slots[30 % 2], op.u.slots[31 % 2], op.m.slots[0], 1.0, net.vref,
+                       op.ws.h[0], st)
+    closure.network_forward(net, op.ws, st)
+    op.op.apply(30, 1, op.dt)
+    fd.fd_cnn_add_correction(op.grid.handle, op.u.slots[31 % 2], op.ws.out, net.rho, st)
+    got = op.u.view(31 % 2).cpu().numpy()
+
+    nxt, _, _ = oracle.acoustic_forward(c["shape"], c["spacing"], cfg["origin"], 4, c["m"], c["eta"], c["dt"], 1,
+                                        src_coords=cfg["src_coords"], src_trace=c["src_trace"], u_cur=uc,
+                                        u_prev=upv, t0=30, n_total=c["nt"])
+    params = [(cnn.bf16_round(w).astype(np.float64), np.zeros(w.shape[2])) for w in net.weights()]
+    corr = cnn.closure_correction(uc, upv, c["m"], params, net.rho, net.vref)
+    ref = nxt + corr
+    # the coarse step agrees to FP32 rounding; the correction to BF16 activations
+    err = np.linalg.norm(got - ref)
+    assert err <= 1e-5 * np.linalg.norm(nxt) + 2e-2 * np.linalg.norm(corr)
+    assert np.linalg.norm(corr) > 0
