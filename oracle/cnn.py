@@ -67,9 +67,11 @@ def conv3d_grad_weight(x, gy):
     return gw, G.sum(axis=0)
 
 
-def network_forward(x, params):
+def network_forward(x, params, store=None):
     """Activations of the 4-layer network; params = [(w, b)] * 4 (b may be
-    zeros: the closure's network has none)."""
+    zeros: the closure's network has none).  `store` (optional) maps every
+    hidden activation to the precision it is stored in between layers (the
+    device keeps them in BF16: store=bf16_round); the output stays FP64."""
     acts = [np.asarray(x, dtype=np.float64)]
     pre = []
     h = acts[0]
@@ -77,20 +79,26 @@ def network_forward(x, params):
         z = conv3d(h, w, b)
         pre.append(z)
         h = np.maximum(z, 0.0) if li < len(params) - 1 else z
+        if store is not None and li < len(params) - 1:
+            h = np.asarray(store(h), dtype=np.float64)
         acts.append(h)
     return acts, pre
 
 
-def network_backward(acts, pre, params, gout):
-    """Gradients of a scalar loss with dL/d(output) = gout: [(gw, gb)] per layer."""
+def network_backward(acts, pre, params, gout, store=None):
+    """Gradients of a scalar loss with dL/d(output) = gout: [(gw, gb)] per layer.
+    `store` (optional) maps every stored gradient dL/dh (gout included) to its
+    storage precision, as network_forward's does for activations; the ReLU
+    derivative is taken from the stored activation (h > 0), which equals z > 0
+    for FP64 storage."""
     grads = [None] * len(params)
-    g = np.asarray(gout, dtype=np.float64)
+    rnd = (lambda a: a) if store is None else (lambda a: np.asarray(store(a), dtype=np.float64))
+    g = rnd(np.asarray(gout, dtype=np.float64))
     for li in range(len(params) - 1, -1, -1):
-        if li < len(params) - 1:
-            g = g * (pre[li] > 0.0)
         gw, gb = conv3d_grad_weight(acts[li], g)
         grads[li] = (gw, gb)
-        g = conv3d_grad_input(g, params[li][0])
+        if li > 0:
+            g = rnd(conv3d_grad_input(g, params[li][0]) * (acts[li] > 0.0))
     return grads
 
 

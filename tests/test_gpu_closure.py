@@ -6,8 +6,10 @@ accumulation over K = 27 taps x 16 channels: |gpu - ref| <= 2e-5 * A, with A
 the same sum taken over absolute values (K * 2^-24 ~ 2.6e-5 bounds the
 relative error of a K-term FP32 sum; the tensor cores' accumulation stays
 within it).  BF16 outputs add one rounding: 2^-8 |ref|.  The whole network
-rounds every activation to BF16 (2^-9 relative each), which the oracle does
-not: gradients agree to a relative L2 error of 2e-2.
+stores every activation and gradient in BF16; against the oracle storing
+them the same way only the accumulation order differs (relative L2 2e-3),
+against the exact FP64 network the BF16 storage costs up to ~3 % at the first
+layer's weight gradient (6e-2 allowed).
 
 Shapes span several CTA tiles in every direction with ragged ends (tiles of
 16 planes x 8 rows x 64 points).
@@ -246,17 +248,25 @@ def test_network_gradients_parity():
     ws_np = [cnn.bf16_round(w).astype(np.float64) for w in net.weights()]
     params = [(w, np.zeros(w.shape[2])) for w in ws_np]
     x = cnn.bf16_round(cnn.features(un, up, mm, 1.5, net.vref).astype(np.float32)).astype(np.float64)
-    acts, pre = cnn.network_forward(x, params)
-    out_ref = acts[-1][..., 0]
     out = ws.out.cpu().numpy().reshape(shape)
-    assert np.linalg.norm(out - out_ref) <= 2e-2 * np.linalg.norm(out_ref)
-    loss_ref, gout = cnn.mse_and_grad(out_ref, tv / 1.5)
-    assert abs(float(ws.loss.item()) - loss_ref) <= 2e-2 * loss_ref
+    got = [net.grad(li).cpu().numpy() for li in range(4)]
+    # (1) the oracle storing activations and gradients in BF16 like the
+    # device: only accumulation order differs
+    acts, pre = cnn.network_forward(x, params, store=cnn.bf16_round)
+    loss_b, gout = cnn.mse_and_grad(acts[-1][..., 0], tv / 1.5)
+    assert np.linalg.norm(out - acts[-1][..., 0]) <= 1e-3 * np.linalg.norm(acts[-1])
+    assert abs(float(ws.loss.item()) - loss_b) <= 1e-4 * loss_b
+    grads = cnn.network_backward(acts, pre, params, gout[..., None], store=cnn.bf16_round)
+    for li in range(4):
+        assert np.linalg.norm(got[li] - grads[li][0]) <= 2e-3 * np.linalg.norm(grads[li][0]), li
+    # (2) the exact FP64 network: BF16 storage costs up to ~3 % at the first
+    # layer's gradient (three BF16 backward stages), so 6e-2
+    acts, pre = cnn.network_forward(x, params)
+    loss_ref, gout = cnn.mse_and_grad(acts[-1][..., 0], tv / 1.5)
+    assert np.linalg.norm(out - acts[-1][..., 0]) <= 1e-2 * np.linalg.norm(acts[-1])
     grads = cnn.network_backward(acts, pre, params, gout[..., None])
     for li in range(4):
-        got = net.grad(li).cpu().numpy()
-        ref = grads[li][0]
-        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref), li
+        assert np.linalg.norm(got[li] - grads[li][0]) <= 6e-2 * np.linalg.norm(grads[li][0]), li
 
 
 def test_closure_step_parity():
