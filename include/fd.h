@@ -277,14 +277,15 @@ fd_status fd_imaging_accumulate(const fd_grid *grid, double scale, const void *m
 /* Tiling of the operator's tiled grid-update kernel (3D acoustic): tiles of
  * at most `rows` rows of d1 by 64 columns of d2, swept along d0, with
  * `stages` planes prefetched (2..4).  0 keeps the planner's choice for that
- * parameter.  Used by the autotuner, which times candidates and keeps the
+ * parameter.  The planner also splits d0 into chunks swept by separate CTAs
+ * when the tile columns alone do not fill the GPU.   Used by the autotuner, which times candidates and keeps the
  * fastest (the GPU analogue of the paper's block-size auto-tuning, Automated
  * code generation section).  Errors: FD_ERR_UNSUPPORTED when the tiling does
  * not fit in shared memory or the operator has no tiled kernel (the previous
  * tiling is kept), FD_ERR_INVALID_ARG. */
 fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stages);
-/* The tiling in use: rows per tile, prefetch depth, CTAs per launch (all 0
- * when the operator runs the plain kernels). */
+/* The tiling in use: rows per tile, prefetch depth, CTAs per launch (tile
+ * columns x d0 chunks; all 0 when the operator runs the plain kernels). */
 fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, int *stages, int *ctas);
 
 /* Autotuner: time candidate tilings (tile heights 8..32 rows by prefetch
@@ -373,9 +374,13 @@ fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, const void *g
  * fd_field_layout): with du = u - u_prev and q = 1/(m vref^2), channels 0..5
  * of x = (u, du, q u, q du, q^2 u, q^2 du) / scale, channels 6..15 = 0 (every
  * channel linear in the wavefield, so that a network without biases is
- * positively homogeneous in it).  x: BF16 activations of grid's shape. */
+ * positively homogeneous in it).  x: BF16 activations of grid's shape.
+ * noise > 0 (training): u and u_prev first get noise * xi added, xi =
+ * sqrt(3) (2 r - 1) with r the top 24 bits of SplitMix64 (Steele, Lea and
+ * Flood 2014) of key `seed` and counter 2p (u) or 2p + 1 (u_prev), p the
+ * point's dense index (i0 n1 + i1) n2 + i2, divided by 2^24. */
 fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m, double scale,
-                          double vref, void *x, void *cuda_stream);
+                          double vref, double noise, uint64_t seed, void *x, void *cuda_stream);
 /* Injection of a fine-grid field into a coarse grid whose nodes are every
  * factor-th fine node: coarse[i, j, k] = fine[f i, f j, f k]; the fine shape
  * must be factor * (n - 1) + 1 per axis (FD_ERR_INVALID_ARG otherwise).  Both

@@ -158,8 +158,8 @@ class ClosureOperator:
         self.eta = fd.DenseData("eta", self.grid)
         self.m.data.copy_(torch.from_numpy(c["m"]))
         self.eta.data.copy_(torch.from_numpy(c["eta"]))
-        self.src = fd.PointData("src", self.grid, cfg["src_coords"], self.nt)
-        self.src.data[:, :1].copy_(torch.from_numpy(c["src_trace"]))
+        self.src = fd.PointData("src", self.grid, c["src_coords"], self.nt)
+        self.src.data[:, : self.src.npoint].copy_(torch.from_numpy(c["src_trace"]))
         self.rec = fd.PointData("rec", self.grid, cfg["rec_coords"], self.nt)
         self.op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, c["space_order"], self.u, self.m, self.eta, src=self.src,
                               rec=self.rec, flags=flags)
@@ -201,8 +201,8 @@ class FineReference:
         self.eta = fd.DenseData("eta", self.grid)
         self.m.data.copy_(torch.from_numpy(f["m"]))
         self.eta.data.copy_(torch.from_numpy(f["eta"]))
-        self.src = fd.PointData("src", self.grid, cfg["src_coords"], self.nt)
-        self.src.data[:, :1].copy_(torch.from_numpy(f["src_trace"]))
+        self.src = fd.PointData("src", self.grid, f["src_coords"], self.nt)
+        self.src.data[:, : self.src.npoint].copy_(torch.from_numpy(f["src_trace"]))
         self.rec = fd.PointData("rec", self.grid, cfg["rec_coords"], self.nt) if receivers else None
         self.op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, f["space_order"], self.u, self.m, self.eta, src=self.src,
                               rec=self.rec, flags=flags)
@@ -247,8 +247,8 @@ class Dataset:
             cm.data.copy_(torch.from_numpy(cs["m"]))
             ce.data.copy_(torch.from_numpy(cs["eta"]))
             cu = fd.TimeData("u", self.cgrid)
-            csrc = fd.PointData("src", self.cgrid, cfg["src_coords"], cs["nt"])
-            csrc.data[:, :1].copy_(torch.from_numpy(cs["src_trace"]))
+            csrc = fd.PointData("src", self.cgrid, cs["src_coords"], cs["nt"])
+            csrc.data[:, : csrc.npoint].copy_(torch.from_numpy(cs["src_trace"]))
             cop = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, cs["space_order"], cu, cm, ce, src=csrc)
             for s in fine.u.slots:
                 s.zero_()
@@ -283,9 +283,14 @@ class Dataset:
         return math.sqrt(float(loss.item()) / self.n)
 
 
-def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None):
+def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None, noise=0.0):
     """Adam on the mean-squared one-step residual error; returns the loss
-    history (one entry per logged iteration, mean over its batch)."""
+    history (one entry per logged iteration, mean over its batch).
+
+    noise > 0 perturbs the input states by noise * s (s the sample's RMS) with
+    unit-variance uniform deviates while the target stays the clean residual,
+    so that the correction does not react to grid-scale content the clean
+    samples never show (which a rollout otherwise amplifies)."""
     torch = net.torch
     ws = Workspace(data.shape)
     g = np.random.default_rng(seed)
@@ -298,7 +303,8 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
         for k in g.integers(0, data.n, size=batch):
             s = float(data.scale[k])
             mod = data.models[data.model_of[k]]
-            fd.fd_cnn_features(data.cgrid.handle, data.states[k, 1], data.states[k, 0], mod, s, net.vref, ws.h[0], st)
+            fd.fd_cnn_features(data.cgrid.handle, data.states[k, 1], data.states[k, 0], mod, s, net.vref, ws.h[0], st,
+                               noise=noise * s, seed=int(g.integers(0, 2 ** 63)))
             network_forward(net, ws, st)
             fd.fd_cnn_mse_grad(data.cgrid.handle, ws.out, data.states[k, 2], data.states[k, 3], s * net.rho, ws.g[0],
                                ws.loss, st)

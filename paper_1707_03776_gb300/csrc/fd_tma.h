@@ -20,6 +20,7 @@ struct TileArgs {
     int n0, n1, n2;      // interior extents
     long long s0, s1;    // element strides of d0 and d1
     int k1, k2;          // tiles along d1 (balanced strips) and d2 (64 wide)
+    int kz;              // chunks of d0 (balanced), each swept by its own CTA
     int rows_max;        // tallest strip
     int box_h;           // rows of a haloed tile: rows_max + 2M
 };

@@ -267,12 +267,31 @@ __global__ void __launch_bounds__(256)
     if (c == 0) atomicAdd(&gb[o], accb);
 }
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output function
+// applied to state = key + (counter + 1) * golden gamma.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long key, unsigned long long counter)
+{
+    unsigned long long z = key + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Unit-variance uniform deviate in [-sqrt 3, sqrt 3) from the top 24 bits.
+__device__ __forceinline__ float unit_uniform(unsigned long long key, unsigned long long counter)
+{
+    const float r = (float)(splitmix64(key, counter) >> 40) * (1.0f / 16777216.0f);
+    return 1.7320508f * (2.f * r - 1.f);
+}
+
 // Closure input features, all linear in the wavefield: with du = u^n -
 // u^{n-1} and q = 1/(m vref^2) (the squared velocity relative to vref),
-// channels 0..5 = (u, du, q u, q du, q^2 u, q^2 du) / s; 6..15 = 0.
+// channels 0..5 = (u, du, q u, q du, q^2 u, q^2 du) / s; 6..15 = 0.  With
+// noise > 0, u^n and u^{n-1} first get noise * xi added, xi the unit-variance
+// deviates of counters 2p and 2p + 1 under key `seed` (training only).
 __global__ void features_kernel(Geom g, const float *__restrict__ u, const float *__restrict__ up,
-                                const float *__restrict__ m, float inv_scale, float inv_vref2,
-                                __nv_bfloat16 *__restrict__ x)
+                                const float *__restrict__ m, float inv_scale, float inv_vref2, float noise,
+                                unsigned long long seed, __nv_bfloat16 *__restrict__ x)
 {
     const long long total = g.n[0] * g.n[1] * g.n[2];
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
@@ -281,7 +300,12 @@ __global__ void features_kernel(Geom g, const float *__restrict__ u, const float
         const long long i2 = p - row * g.n[2];
         const long long i0 = row / g.n[1], i1 = row - i0 * g.n[1];
         const long long at = i0 * g.s0 + i1 * g.s1 + i2;
-        const float a = u[at] * inv_scale, b = (u[at] - up[at]) * inv_scale;
+        float uc = u[at], uq = up[at];
+        if (noise != 0.f) {
+            uc += noise * unit_uniform(seed, 2ull * (unsigned long long)p);
+            uq += noise * unit_uniform(seed, 2ull * (unsigned long long)p + 1ull);
+        }
+        const float a = uc * inv_scale, b = (uc - uq) * inv_scale;
         const float q = inv_vref2 / m[at];
         __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(x + p * kC);
         dst[0] = __floats2bfloat162_rn(a, b);
@@ -480,14 +504,16 @@ extern "C" fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, co
 }
 
 extern "C" fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m,
-                                     double scale, double vref, void *x, void *stream)
+                                     double scale, double vref, double noise, uint64_t seed, void *x, void *stream)
 {
-    if (!grid || grid->ndim != 3 || !u || !u_prev || !m || !x || !(scale > 0) || !(vref > 0))
+    if (!grid || grid->ndim != 3 || !u || !u_prev || !m || !x || !(scale > 0) || !(vref > 0) ||
+        !(noise >= 0))
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_features: bad arguments");
     const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     features_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-        g, u, u_prev, m, (float)(1.0 / scale), (float)(1.0 / (vref * vref)), (__nv_bfloat16 *)x);
+        g, u, u_prev, m, (float)(1.0 / scale), (float)(1.0 / (vref * vref)), (float)noise,
+        (unsigned long long)seed, (__nv_bfloat16 *)x);
     CNN_CUDA(cudaGetLastError(), "fd_cnn_features");
     return FD_OK;
 }

@@ -149,13 +149,15 @@ __device__ inline void init_barriers(const SweepSmem &sm)
     __syncthreads();
 }
 
-// Sweep tile `tile` of one grid.  it_u / it_a count the u^n and aux loads this
-// CTA has consumed so far (ring slots and barrier phases continue across
-// columns).  Returns false when a wait gave up (status set, copies drained).
+// Sweep output planes [z_lo, z_hi) of tile `tile` of one grid (the first 2M
+// iterations only load the u^n planes z_lo-M .. z_lo+M-1 that the first
+// output plane reads).  it_u / it_a count the u^n and aux loads this CTA has
+// consumed so far (ring slots and barrier phases continue across columns).
+// Returns false when a wait gave up (status set, copies drained).
 template <int M, int P>
 __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
                              const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
-                             int tile, const SrcEntry *__restrict__ src_tab, int nsrc,
+                             int tile, int z_lo, int z_hi, const SrcEntry *__restrict__ src_tab, int nsrc,
                              const float *__restrict__ src_row, const SweepSmem &sm, unsigned &it_u, unsigned &it_a,
                              int *status)
 {
@@ -174,7 +176,7 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
     const int r = tid >> 4;
     const int qc = tid & 15;
     const bool active = r < rows && col0 + 4 * qc < a.n2;
-    const int J = a.n0 + 2 * M;
+    const int J = (z_hi - z_lo) + 2 * M;
     const int plane_u = sm.plane_u, plane_a = sm.plane_a;
     float *ring = sm.ring;
     float *aux = sm.aux;
@@ -183,23 +185,23 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
     const uint32_t bytes_a = (uint32_t)(3 * a.rows_max * kTileW * sizeof(float));
     const unsigned iu = it_u, ia = it_a;
 
-    // iteration j: u^n plane j-M into ring slot (iu+j) % NU; for j >= 2M the
-    // aux of output plane j-2M into aux slot (ia+j-2M) % NA
+    // iteration j: u^n plane z_lo-M+j into ring slot (iu+j) % NU; for j >= 2M
+    // the aux of output plane z_lo+j-2M into aux slot (ia+j-2M) % NA
     auto issue = [&](int j) {
         const unsigned gu = iu + (unsigned)j;
         const int su = (int)(gu % NU);
         const uint32_t bu = smem_addr(&bars[su]);
         mbar_expect_tx(bu, bytes_u);
-        tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, j - M, bu);
+        tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, z_lo - M + j, bu);
         if (j >= 2 * M) {
             const int ja = j - 2 * M;
             const int sa = (int)((ia + (unsigned)ja) % NA);
             const uint32_t ba = smem_addr(&bars[NU + sa]);
             float *dst = aux + sa * 3 * plane_a;
             mbar_expect_tx(ba, bytes_a);
-            tma_load_3d(smem_addr(dst), map_um, col0, row0, ja, ba);
-            tma_load_3d(smem_addr(dst + plane_a), map_c, col0, row0, ja, ba);
-            tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, ja, ba);
+            tma_load_3d(smem_addr(dst), map_um, col0, row0, z_lo + ja, ba);
+            tma_load_3d(smem_addr(dst + plane_a), map_c, col0, row0, z_lo + ja, ba);
+            tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, z_lo + ja, ba);
         }
     };
     auto wait_u = [&](int j) {
@@ -250,7 +252,8 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
         q[Q - 1] = *reinterpret_cast<const float4 *>(ring + ((iu + j) % NU) * plane_u + (r + M) * kBoxW + kSideHalo +
                                                      4 * qc);
         if (j >= 2 * M) {
-            const int ja = j - 2 * M;  // output plane
+            const int ja = j - 2 * M;  // output plane z_lo + ja
+            const int zo = z_lo + ja;
             ok = wait_a(ja) && ok;
             if (ok && active) {
                 const float *pc =
@@ -298,8 +301,8 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
                 if (nsrc > 0) {
                     // source injection at the corners this thread owns on plane ja
                     float inj0 = 0.f, inj1 = 0.f, inj2 = 0.f, inj3 = 0.f;
-                    const int s_end = s_sstart[ja + 1];
-                    for (int k = s_sstart[ja]; k < s_end; k++) {
+                    const int s_end = s_sstart[zo + 1];
+                    for (int k = s_sstart[zo]; k < s_end; k++) {
                         const SrcEntry e = s_src[k];
                         if (e.r == r && (e.x >> 2) == qc) {
                             const float sv = e.w * src_row[e.p];
@@ -315,7 +318,7 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
                     res[2] = fmaf(inj2, cv[2], res[2]);
                     res[3] = fmaf(inj3, cv[3], res[3]);
                 }
-                float *o = out + (long long)ja * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
+                float *o = out + (long long)zo * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
                 if (col0 + 4 * qc + 3 < a.n2) {
                     *reinterpret_cast<float4 *>(o) = make_float4(res[0], res[1], res[2], res[3]);
                 } else {
@@ -348,7 +351,7 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
         return false;
     }
     it_u = iu + (unsigned)J;
-    it_a = ia + (unsigned)a.n0;
+    it_a = ia + (unsigned)(z_hi - z_lo);
     return true;
 }
 

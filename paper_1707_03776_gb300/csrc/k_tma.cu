@@ -16,10 +16,11 @@
 // gives up, the CTA records FD_ERR_TIMEOUT in the operator's status word and
 // leaves after draining its own copies.
 //
-// The grid has one CTA per tile, and the planner sizes the tiles so that the
-// tile count matches the SM count (152 on GB300): all CTAs sweep d0 together,
-// so the halo rows a CTA loads were just loaded by its neighbour and are
-// served from L2.
+// The grid has one CTA per tile and d0 chunk, and the planner sizes the
+// tiles (and, for grids too small to fill the GPU with columns, splits d0
+// into chunks) so that the CTA count matches the resident slots of the 152
+// SMs: all CTAs sweep together, so the halo rows a CTA loads were just loaded
+// by its neighbour and are served from L2.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -55,12 +56,17 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
         prefetch_map(&map_d);
     }
     init_barriers<M, P>(sm);
-    const int tile = blockIdx.x;
+    // CTA = (d0 chunk, tile column); chunks are balanced ranges of planes
+    const int ncol = a.k1 * a.k2;
+    const int tile = (int)(blockIdx.x % (unsigned)ncol);
+    const int chunk = (int)(blockIdx.x / (unsigned)ncol);
+    const int z_lo = (int)((long long)chunk * a.n0 / a.kz);
+    const int z_hi = (int)((long long)(chunk + 1) * a.n0 / a.kz);
     const int s0 = src_row ? src_off[tile] : 0;
     const int nsrc = src_row ? src_off[tile + 1] - s0 : 0;
     unsigned it_u = 0, it_a = 0;
-    sweep_column<M, P>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, src_tab + s0, nsrc, src_row, sm, it_u,
-                       it_a, status);
+    sweep_column<M, P>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc, src_row,
+                       sm, it_u, it_a, status);
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -152,31 +158,59 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     // work of the busiest SM, ceil(ctas / SMs) tiles of rows + M/2 row-planes
     // (halo rows cost TMA traffic, served mostly from L2), with every tile of
     // one wave resident at once; ties go to taller tiles.
-    int best_k1 = -1;
+    // The d0 chunk count kz multiplies the CTAs only for grids whose columns
+    // alone leave SMs idle (up to the resident slots of all SMs); a chunk
+    // costs its planes plus the 2M it loads before its first output plane
+    // (weighted 0.35: u^n is one of the four streams).  Chunks keep at least
+    // 4M planes.
+    const int kz_lim = std::max(1, std::min(64, a.n0 / std::max(4 * M, 8)));
+    auto kz_cap = [&](int k1, int occ) {
+        const long long cols = (long long)k1 * a.k2;
+        if (cols >= sms) return 1;
+        return (int)std::min<long long>(kz_lim, ((long long)sms * occ + cols - 1) / cols);
+    };
+    auto cost_of = [&](int k1, int kz, int occ) {
+        const int rows_max = (a.n1 + k1 - 1) / k1;
+        const long long ctas = (long long)k1 * a.k2 * kz;
+        const long long per_sm = (ctas + sms - 1) / sms;
+        const long long waves = (per_sm + occ - 1) / occ;
+        const double planes = (double)((a.n0 + kz - 1) / kz) + 0.35 * 2 * M;
+        return (double)waves * occ * (rows_max + 0.5 * M) * planes * (per_sm > occ ? 1.0 : (double)per_sm / occ);
+    };
+    int best_k1 = -1, best_kz = 1;
     double best_cost = 0;
     if (want_rows > 0) {
         const int k1 = (a.n1 + want_rows - 1) / want_rows;
-        if (want_rows > kMaxRows || occupancy((a.n1 + k1 - 1) / k1, kMinStages) < 1)
+        const int occ = occupancy((a.n1 + k1 - 1) / k1, kMinStages);
+        if (want_rows > kMaxRows || occ < 1)
             return set_error(FD_ERR_UNSUPPORTED, "tiling: %d rows per tile do not fit", want_rows);
         best_k1 = k1;
+        for (int kz = 1; kz <= kz_cap(k1, occ); kz++) {
+            const double cost = cost_of(k1, kz, occ);
+            if (kz == 1 || cost < best_cost - 1e-9) {
+                best_kz = kz;
+                best_cost = cost;
+            }
+        }
     } else {
         for (int k1 = (a.n1 + kMaxRows - 1) / kMaxRows; k1 <= a.n1; k1++) {
             const int rows_max = (a.n1 + k1 - 1) / k1;
             const int occ = occupancy(rows_max, kMinStages);
             if (occ < 1) continue;
-            const long long ctas = (long long)k1 * a.k2;
-            const long long per_sm = (ctas + sms - 1) / sms;
-            const long long waves = (per_sm + occ - 1) / occ;
-            const double cost = (double)waves * occ * (rows_max + 0.5 * M) * (per_sm > occ ? 1.0 : (double)per_sm / occ);
-            if (best_k1 < 0 || cost < best_cost - 1e-9) {
-                best_k1 = k1;
-                best_cost = cost;
+            for (int kz = 1; kz <= kz_cap(k1, occ); kz++) {
+                const double cost = cost_of(k1, kz, occ);
+                if (best_k1 < 0 || cost < best_cost - 1e-9) {
+                    best_k1 = k1;
+                    best_kz = kz;
+                    best_cost = cost;
+                }
             }
-            if (ctas > 8LL * sms) break;
+            if ((long long)k1 * a.k2 > 8LL * sms) break;
         }
     }
     if (best_k1 < 0) return FD_OK;  // tiles do not fit: plain kernels
     a.k1 = best_k1;
+    a.kz = best_kz;
     a.rows_max = (a.n1 + a.k1 - 1) / a.k1;
     a.box_h = a.rows_max + 2 * M;
 
@@ -331,14 +365,14 @@ void tma_plan_tiling(const TmaPlan &plan, int *rows, int *stages, int *ctas)
 {
     *rows = plan.ready ? plan.args.rows_max : 0;
     *stages = plan.ready ? plan.stages : 0;
-    *ctas = plan.ready ? plan.args.k1 * plan.args.k2 : 0;
+    *ctas = plan.ready ? plan.args.k1 * plan.args.k2 * plan.args.kz : 0;
 }
 
 static cudaError_t launch_maps(const TmaPlan &plan, int M, const Coef &cf, const CUtensorMap &map_cur,
                                const CUtensorMap &map_prev, float *out, int *status, const float *src_row,
                                cudaStream_t st)
 {
-    dim3 grid((unsigned)(plan.args.k1 * plan.args.k2));
+    dim3 grid((unsigned)(plan.args.k1 * plan.args.k2 * plan.args.kz));
     dim3 block((unsigned)plan.threads);
     const float *srow = plan.has_src ? src_row : nullptr;
     const int key = M * 8 + plan.stages;

@@ -279,22 +279,27 @@ def layered_velocity(shape, spacing, seed, vmin=1500.0, vmax=3500.0, extent=None
 
 
 def closure_config(n_coarse=48, nt=400, seed=0, sponge=8, f0=8.0, vmin=1500.0, vmax=3500.0, cfl=0.3,
-                   src="random", nrec_side=None):
+                   src="random", src_sigma=30.0, nrec_side=None):
     """One learned-closure experiment: the same layered model, source and
     receivers on a coarse grid (n_coarse^3 nodes at 20 m, SO4) and on the fine
     grid whose every other node is a coarse node ((2 n_coarse - 1)^3 at 10 m,
     SO16).  dt_fine = cfl * 10 m / vmax and dt_coarse = 2 dt_fine (the same
     Courant number on both grids); the fine run takes 2 nt steps.
 
-    The source sits on a coarse node: a random interior node (src="random") or
-    the centre of the top face just below the sponge (src="surface").  The
-    Ricker amplitude is divided by each grid's cell volume (the injection adds
-    amplitude * dt^2/m at the nodes, so this discretises one point source of
-    unit strength on both grids).  Receivers: a square lattice of coarse nodes
-    (every other one) on the plane one coarse cell below the source depth of
-    a surface source.  Sponges of `sponge` coarse cells (twice as many fine
-    cells) with sigma_max of a 20-coarse-cell layer: the same physical
-    profile on both grids."""
+    The source is a Gaussian density (standard deviation `src_sigma` m, cut
+    at 2.5 sigma and normalised to unit strength on each grid: sum of density
+    times cell volume = 1) times a Ricker wavelet, injected at every node of
+    each grid within the cut with amplitude density(node) * wavelet(t)
+    (the injection adds amplitude * dt^2/m, so per-node densities discretise
+    the same source on both grids).  A smooth source keeps the wavefield free
+    of grid-scale content that the coarse grid cannot represent.  The centre
+    sits on a coarse node: random in the interior (src="random") or at the
+    centre of the top face 6 coarse cells below the sponge (src="surface").
+    Receivers: a square lattice of coarse nodes (every other one) on the
+    plane 3 coarse cells above the bottom sponge, so that every receiver is
+    far from the source and its trace error measures propagation.  Sponges of `sponge` coarse cells
+    (twice as many fine cells) with sigma_max of a 400 m layer: the same
+    physical profile on both grids."""
     g = np.random.default_rng(SEED_BASE + 104729 * seed + 1)
     hc, hf = 20.0, 10.0
     nc = int(n_coarse)
@@ -315,24 +320,38 @@ def closure_config(n_coarse=48, nt=400, seed=0, sponge=8, f0=8.0, vmin=1500.0, v
 
     m_c, eta_c = fields(v_c, shape_c, sp_c, sponge)
     m_f, eta_f = fields(v_f, shape_f, sp_f, 2 * sponge)
-    lo, hi = sponge + 4, nc - 1 - sponge - 4
+    reach = int(math.ceil(2.5 * src_sigma / hc))
+    lo, hi = sponge + reach + 1, nc - 1 - sponge - reach - 1
     if src == "random":
         s_idx = g.integers(lo, hi + 1, size=3).astype(np.float64)
     else:
-        s_idx = np.array([(nc - 1) // 2, (nc - 1) // 2, sponge + 2], dtype=np.float64)
-    src_coords = (s_idx * hc).reshape(1, 3)
+        s_idx = np.array([(nc - 1) // 2, (nc - 1) // 2, sponge + 6], dtype=np.float64)
+    centre = s_idx * hc
+
+    def gaussian_source(h, n_steps, dt):
+        r = int(math.ceil(2.5 * src_sigma / h))
+        k = np.arange(-r, r + 1, dtype=np.float64)
+        K0, K1, K2 = np.meshgrid(k, k, k, indexing="ij")
+        d2 = (K0 ** 2 + K1 ** 2 + K2 ** 2) * h * h
+        keep = d2 <= (2.5 * src_sigma) ** 2
+        coords = centre + np.stack([K0[keep], K1[keep], K2[keep]], axis=1) * h
+        dens = np.exp(-d2[keep] / (2.0 * src_sigma ** 2))
+        dens /= dens.sum() * h ** 3  # unit strength on each grid: sum of density * cell volume = 1
+        trace = ricker(n_steps, dt, f0)[:, None] * dens[None, :]
+        return coords, trace.astype(np.float32)
+
+    src_c, trace_c = gaussian_source(hc, nt, dt_c)
+    src_f, trace_f = gaussian_source(hf, 2 * nt, dt_f)
     side = np.arange(sponge + 1, nc - sponge - 1, 2, dtype=np.float64)
     if nrec_side is not None:
         side = side[:: max(1, side.size // int(nrec_side))][: int(nrec_side)]
     X, Y = np.meshgrid(side, side, indexing="ij")
-    depth = float(sponge + 3)
+    depth = float(nc - 1 - sponge - 3)
     rec_coords = np.stack([X.ravel(), Y.ravel(), np.full(X.size, depth)], axis=1) * hc
-    w_c = ricker(nt, dt_c, f0) / hc ** 3
-    w_f = ricker(2 * nt, dt_f, f0) / hf ** 3
     return dict(
         coarse=dict(shape=shape_c, spacing=sp_c, space_order=4, dt=dt_c, nt=nt, m=m_c, eta=eta_c,
-                    src_trace=w_c.astype(np.float32).reshape(nt, 1)),
+                    src_coords=src_c, src_trace=trace_c),
         fine=dict(shape=shape_f, spacing=sp_f, space_order=16, dt=dt_f, nt=2 * nt, m=m_f, eta=eta_f,
-                  src_trace=w_f.astype(np.float32).reshape(2 * nt, 1)),
-        origin=(0.0, 0.0, 0.0), src_coords=src_coords, rec_coords=rec_coords, vmax=vmax, vmin=vmin, f0=f0,
-        sponge=sponge, seed=seed)
+                  src_coords=src_f, src_trace=trace_f),
+        origin=(0.0, 0.0, 0.0), rec_coords=rec_coords, vmax=vmax, vmin=vmin, f0=f0, sponge=sponge, seed=seed,
+        src_centre=centre)

@@ -185,8 +185,9 @@ def test_rebind_by_name():
 
 
 def test_tilings_agree_bitwise_and_autotune():
-    """Every tiling (tile height, prefetch depth) computes the same per-point
-    arithmetic, so results agree bit for bit; the autotuner picks one of them."""
+    """Every tiling (tile height, prefetch depth, d0 chunks) computes the same
+    per-point arithmetic, so results agree bit for bit; the autotuner picks
+    one of them."""
     cfg = wl.acoustic_config(n=72, space_order=8, nt=30, sponge=8, nrec_side=7)
     args = (cfg["shape"], cfg["spacing"], cfg["origin"], 8, cfg["m"], cfg["eta"], cfg["src_coords"],
             cfg["src_trace"], cfg["rec_coords"], cfg["nt"])
@@ -198,6 +199,9 @@ def test_tilings_agree_bitwise_and_autotune():
         assert r > 0 and s >= 2 and ctas > 0
         if rows:
             assert r <= rows and s == stages
+            # 72 planes of 2 x ceil(72/r) columns do not fill the GPU: the
+            # planner splits d0 into chunks swept by separate CTAs
+            assert ctas >= 2 * (2 * -(-72 // r))
         run.run(0, 30, cfg["dt"])
         results.append((run.state(30)[0], run.rec_trace()))
     for u, rec in results[1:]:

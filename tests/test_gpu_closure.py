@@ -172,6 +172,12 @@ def test_features_restrict_correction_mse_adam():
     got = x.float().cpu().numpy().reshape(shape + (16,))
     assert np.all(np.abs(got[..., :6] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6 * np.abs(ref).max())
     assert np.all(got[..., 6:] == 0.0)
+    # the training-time noise: SplitMix64 deviates on both sides
+    fd.fd_cnn_features(grid.handle, u.slots[0], u.slots[1], m.slots[0], 2.0, 3000.0, x, st, noise=0.3, seed=777)
+    nu, nup = cnn.noisy_states(un, up, 0.3, 777)
+    ref = cnn.features(nu, nup, mm, 2.0, 3000.0)
+    got = x.float().cpu().numpy().reshape(shape + (16,))
+    assert np.all(np.abs(got[..., :6] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max())
 
     # restriction from a (2n-1)-node fine grid, with the sum of squares
     fshape = tuple(2 * s - 1 for s in shape)
@@ -294,7 +300,7 @@ def test_closure_step_parity():
     got = op.u.view(31 % 2).cpu().numpy()
 
     nxt, _, _ = oracle.acoustic_forward(c["shape"], c["spacing"], cfg["origin"], 4, c["m"], c["eta"], c["dt"], 1,
-                                        src_coords=cfg["src_coords"], src_trace=c["src_trace"], u_cur=uc,
+                                        src_coords=c["src_coords"], src_trace=c["src_trace"], u_cur=uc,
                                         u_prev=upv, t0=30, n_total=c["nt"])
     params = [(cnn.bf16_round(w).astype(np.float64), np.zeros(w.shape[2])) for w in net.weights()]
     corr = cnn.closure_correction(uc, upv, c["m"], params, net.rho, net.vref)

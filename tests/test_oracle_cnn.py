@@ -153,3 +153,16 @@ def test_bias_free_network_is_homogeneous():
     b = cnn.closure_correction(7.5 * u, 7.5 * up, m, params, 0.5, 3000.0)
     np.testing.assert_allclose(b, 7.5 * a, rtol=1e-12, atol=1e-14)
     assert np.all(cnn.closure_correction(0 * u, 0 * up, m, params, 0.5, 3000.0) == 0.0)
+
+
+def test_splitmix64_published_vector():
+    """SplitMix64 against the published first outputs for seed 1234567
+    (golden splitmix64.txt), and the unit-variance deviates' range/moments."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+    want = [int(line) for line in open(path) if line.strip() and not line.startswith("#")]
+    got = [int(cnn.splitmix64(1234567, i)) for i in range(len(want))]
+    assert got == want
+    xi = cnn.unit_uniform(99, np.arange(200000, dtype=np.uint64))
+    assert xi.min() >= -np.sqrt(3.0) and xi.max() < np.sqrt(3.0)
+    assert abs(xi.mean()) < 0.01 and abs(xi.var() - 1.0) < 0.01
