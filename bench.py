@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=3, help="time steps in the CPU-oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-rows", action="store_true", help="skip the secondary rows (2D diffusion)")
+    p.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
+    p.add_argument("--rows", default="diffusion,gradient,batched,learned",
+                   help="secondary rows to run (comma-separated)")
     p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
     p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel (default: autotuned)")
     return p.parse_args()
@@ -173,6 +175,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+def measured_peak_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
 
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -374,6 +385,78 @@ def bench_batched(nshots=64, nt=800, plain_shots=8):
             "launches_per_step": 1, "window_points": pts / nt}
 
 
+def bench_learned(n=128, nt=2000):
+    """The learned-closure row: a coarse 20 m SO4 grid corrected every step
+    by the 4-layer BF16 CNN, trained on 128 fine-grid (10 m, SO16) runs of
+    seeded layered models, evaluated on an unseen layered model on a 256^3-
+    equivalent domain (128^3 coarse, 255^3 fine nodes) for 2000 coarse steps.
+    Receiver-trace errors are relative to the plain fine-grid run (the
+    judge); the plain coarse grid at SO 4/8/16 shows what the spatial order
+    alone buys at 20 m.  Wall times include every launch of the run (the
+    network, the coarse update, the correction)."""
+    import numpy as np
+    import torch
+    from paper_1707_03776_gb300 import closure
+    from paper_1707_03776_gb300 import workloads as wl
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    (net, data, hist), t_train = timed(lambda: closure.train_default(log_every=200))
+    cfg = wl.closure_config(n, nt, seed=1001, src="surface")
+    fine = closure.FineReference(cfg)
+    fine.run(20)
+    ref, t_fine = timed(lambda: fine.run().cpu().numpy())
+    del fine
+    plain = {}
+    for so in (4, 8, 16):
+        c2 = dict(cfg)
+        c2["coarse"] = dict(cfg["coarse"], space_order=so)
+        op = closure.ClosureOperator(c2, net)
+        op.run(20, learned=False)
+        tr, t = timed(lambda: op.run(learned=False).cpu().numpy())
+        plain["SO%d" % so] = {"trace_rel_err": closure.trace_error(tr, ref), "s": t}
+        del op
+    op = closure.ClosureOperator(cfg, net)
+    op.run(20)
+    lr_tr, t_learned = timed(lambda: op.run().cpu().numpy())
+    err = closure.trace_error(lr_tr, ref)
+    # the network alone: CUDA events around its launches
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        closure.network_forward(net, op.ws, st.cuda_stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(st)
+    for _ in range(reps):
+        closure.network_forward(net, op.ws, st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_net = e0.elapsed_time(e1) / reps
+    pts = float(n) ** 3
+    ch = closure.CHANNELS
+    flops = 2.0 * 27 * pts * sum(ch[i] * ch[i + 1] for i in range(len(ch) - 1))
+    flops_mma = 2.0 * 27 * pts * 16 * (16 * 3 + 8)  # K padded to 16 channels, the last layer's N to 8
+    peak, kind = measured_peak_bf16()
+    achieved = flops / (ms_net * 1e-3) / 1e12
+    return {"workload": "closure_coarse%d^3_20m_so4_fine%d^3_10m_so16_nt%d_layered" % (n, 2 * n - 1, nt),
+            "unit": "s per modelled shot; trace errors relative to the fine grid",
+            "trace_rel_err_learned": err, "trace_rel_err_plain_coarse": plain,
+            "s_learned": t_learned, "s_fine_grid": t_fine,
+            "learned_vs_fine_time": t_learned / t_fine,
+            "train": {"s": t_train, "samples": data.n, "models": 128, "iters": 800, "rho": net.rho,
+                      "loss_first_last": [hist[0][1], hist[-1][1]]},
+            "network_ms_per_step": ms_net, "network_share_of_learned_step": ms_net * nt / 1e3 / t_learned,
+            "roofline": {"bound": "tensor", "kernel": "conv3d (implicit GEMM, mma.sync m16n8k16 BF16/FP32)",
+                         "achieved": achieved, "achieved_mma_issued": flops_mma / (ms_net * 1e-3) / 1e12,
+                         "peak": peak, "peak_kind": kind, "unit": "TFLOP/s", "frac": achieved / peak}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -495,7 +578,9 @@ def run_ours(args):
 
     rows = None
     if rank == 0 and not args.no_rows:
-        rows = {"diffusion": bench_diffusion(), "gradient": bench_gradient(), "batched": bench_batched()}
+        fns = {"diffusion": bench_diffusion, "gradient": bench_gradient, "batched": bench_batched,
+               "learned": bench_learned}
+        rows = {name: fns[name]() for name in args.rows.split(",") if name in fns}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world, "steps": args.steps,

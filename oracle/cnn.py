@@ -18,6 +18,8 @@ conv(16 -> 1), no biases; the closure adds rho times its output to the coarse
 update.  Also here: the closure's input features, the fine-to-coarse
 injection, the training loss and Adam (Kingma and Ba 2015, Algorithm 1).
 """
+import math
+
 import numpy as np
 
 TAPS = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
@@ -118,6 +120,31 @@ def features(u, u_prev, m, scale, vref):
     du = u - np.asarray(u_prev, dtype=np.float64)
     q = 1.0 / (np.asarray(m, dtype=np.float64) * vref * vref)
     return np.stack([u, du, q * u, q * du, q * q * u, q * q * du], axis=-1) / scale
+
+
+def splitmix64(key, counter):
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) output for state
+    key + (counter + 1) * 0x9E3779B97F4A7C15 (uint64 arrays)."""
+    M = np.uint64(0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):
+        z = (np.uint64(key) + (np.asarray(counter, dtype=np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)) & M
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & M
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & M
+    return z ^ (z >> np.uint64(31))
+
+
+def unit_uniform(key, counter):
+    """Unit-variance uniform deviates sqrt(3) (2 r - 1), r = top 24 bits / 2^24."""
+    r = (splitmix64(key, counter) >> np.uint64(40)).astype(np.float64) / 16777216.0
+    return math.sqrt(3.0) * (2.0 * r - 1.0)
+
+
+def noisy_states(u, u_prev, noise, seed):
+    """The training-time perturbation of the closure's input states: point p
+    (dense index) gets noise * xi(2p) and noise * xi(2p + 1)."""
+    p = np.arange(np.asarray(u).size, dtype=np.uint64).reshape(np.shape(u))
+    return (np.asarray(u, dtype=np.float64) + noise * unit_uniform(seed, 2 * p),
+            np.asarray(u_prev, dtype=np.float64) + noise * unit_uniform(seed, 2 * p + np.uint64(1)))
 
 
 def restrict(fine, factor):

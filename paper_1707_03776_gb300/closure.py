@@ -317,6 +317,20 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
     return hist
 
 
+def train_default(count=128, n_coarse=64, nt=600, iters=800, seed=0, log_every=0):
+    """The closure as trained for the evaluation workload: a dataset of
+    `count` layered-model runs (workloads.closure_training_set), rho from the
+    dataset, 800 Adam iterations of batch 4 with a cosine learning rate from
+    2e-3 to 5e-5 (longer training lowered the one-step loss but not the
+    rollout error).  Returns (net, dataset, loss history)."""
+    from . import workloads as wl
+    cfgs, steps = wl.closure_training_set(count, n_coarse, nt)
+    data = Dataset(cfgs, steps)
+    net = ClosureNet(seed=seed, rho=data.residual_ratio())
+    hist = train(net, data, iters, batch=4, lr=2e-3, lr_final=5e-5, seed=seed, log_every=log_every)
+    return net, data, hist
+
+
 def trace_error(traces, reference):
     """Relative L2 error of receiver traces against the fine-grid traces."""
     a = np.asarray(traces, dtype=np.float64)

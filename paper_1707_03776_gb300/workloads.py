@@ -355,3 +355,13 @@ def closure_config(n_coarse=48, nt=400, seed=0, sponge=8, f0=8.0, vmin=1500.0, v
                   src_coords=src_f, src_trace=trace_f),
         origin=(0.0, 0.0, 0.0), rec_coords=rec_coords, vmax=vmax, vmin=vmin, f0=f0, sponge=sponge, seed=seed,
         src_centre=centre)
+
+
+def closure_training_set(count=128, n_coarse=64, nt=600, f0=8.0, first=160, every=40):
+    """The closure's training experiments: `count` seeded layered models
+    (seeds 0..count-1, random interior sources) on n_coarse^3 coarse grids,
+    and the coarse steps sampled from each fine run: every `every` steps from
+    `first` (after the 2/f0 s the source lasts, so that the network, which
+    does not see the source, learns the propagation error)."""
+    cfgs = [closure_config(n_coarse, nt, seed=s, f0=f0) for s in range(count)]
+    return cfgs, list(range(first, nt - 2, every))

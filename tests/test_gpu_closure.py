@@ -309,3 +309,50 @@ def test_closure_step_parity():
     err = np.linalg.norm(got - ref)
     assert err <= 1e-5 * np.linalg.norm(nxt) + 2e-2 * np.linalg.norm(corr)
     assert np.linalg.norm(corr) > 0
+
+
+def test_closure_rollout_parity():
+    """40 learned steps from rest on the GPU against the oracle's coarse steps
+    plus the oracle network's correction (FP64 network on the same BF16
+    weights).  The correction is ~rho of the field, so its BF16 storage error
+    is ~1e-2 of rho relative: the traces agree to 1e-4."""
+    torch = _torch()
+    import oracle
+    from paper_1707_03776_gb300 import closure, workloads as wl
+    cfg = wl.closure_config(n_coarse=20, nt=40, seed=9, sponge=3, src_sigma=25.0)
+    c = cfg["coarse"]
+    net = closure.ClosureNet(seed=7, rho=0.01)
+    op = closure.ClosureOperator(cfg, net)
+    got = op.run(40).cpu().numpy().copy()
+    params = [(cnn.bf16_round(w).astype(np.float64), np.zeros(w.shape[2])) for w in net.weights()]
+    uc = np.zeros(c["shape"])
+    up = np.zeros(c["shape"])
+    rec = np.zeros_like(got, dtype=np.float64)
+    for n in range(40):
+        corr = cnn.closure_correction(uc, up, c["m"], params, net.rho, net.vref)
+        nxt, _, tr = oracle.acoustic_forward(c["shape"], c["spacing"], cfg["origin"], 4, c["m"], c["eta"], c["dt"],
+                                             1, src_coords=c["src_coords"], src_trace=c["src_trace"],
+                                             rec_coords=cfg["rec_coords"], u_cur=uc, u_prev=up, t0=n,
+                                             n_total=c["nt"])
+        rec[n] = tr[n]
+        up, uc = uc, nxt + corr
+    assert np.linalg.norm(got - rec) <= 1e-4 * np.linalg.norm(rec)
+    plain = op.run(40, learned=False).cpu().numpy()
+    assert np.linalg.norm(plain - rec) > 10 * np.linalg.norm(got - rec)  # the correction is visible
+
+
+def test_training_lowers_loss_and_trace_error():
+    """Training on 32 layered-model runs lowers the one-step loss, and the
+    trained closure's receiver traces are closer to the fine grid's than the
+    plain coarse run's on an unseen model (smaller than the evaluation
+    workload; the full-size numbers come from bench.py)."""
+    _torch()
+    from paper_1707_03776_gb300 import closure, workloads as wl
+    net, data, hist = closure.train_default(count=32, n_coarse=48, nt=500, iters=600, log_every=100)
+    assert hist[-1][1] < 0.1 * hist[0][1]
+    cfg = wl.closure_config(64, 800, seed=1000, src="surface")
+    ref = closure.FineReference(cfg).run().cpu().numpy()
+    op = closure.ClosureOperator(cfg, net)
+    plain = closure.trace_error(op.run(learned=False).cpu().numpy(), ref)
+    learned = closure.trace_error(op.run(learned=True).cpu().numpy(), ref)
+    assert np.isfinite(learned) and learned < 0.85 * plain, (learned, plain)
