@@ -285,7 +285,8 @@ class Dataset:
 
 def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None, noise=0.0):
     """Adam on the mean-squared one-step residual error; returns the loss
-    history (one entry per logged iteration, mean over its batch).
+    history: (iteration, mean loss per sample over the iterations since the
+    previous entry) every `log_every` iterations and at the last.
 
     noise > 0 perturbs the input states by noise * s (s the sample's RMS) with
     unit-variance uniform deviates while the target stays the clean residual,
@@ -297,9 +298,11 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
     st = _stream()
     hist = []
     lr_final = lr if lr_final is None else lr_final
+    ws.loss.zero_()
+    since = 0
     for it in range(iters):
         net.grads.zero_()
-        ws.loss.zero_()
+        since += 1
         for k in g.integers(0, data.n, size=batch):
             s = float(data.scale[k])
             mod = data.models[data.model_of[k]]
@@ -313,7 +316,9 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
         a = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * it / max(iters - 1, 1)))
         net.adam(a)
         if log_every and (it % log_every == 0 or it == iters - 1):
-            hist.append((it, float(ws.loss.item()) / batch))
+            hist.append((it, float(ws.loss.item()) / (batch * since)))
+            ws.loss.zero_()
+            since = 0
     return hist
 
 

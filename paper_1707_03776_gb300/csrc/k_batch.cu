@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
                           const long long n, const int cur, int *status)
 {
     if (*reinterpret_cast<volatile int *>(status) != 0) return;
+    // everything but the per-plane starts (checked per shot below)
+    if (!smem_fits<M, P>(rows_max, src_cap, 0, status)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SweepSmem sm = carve_smem<M, P>(smem_raw, rows_max, src_cap);
     init_barriers<M, P>(sm);
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
         const ShotDesc *sd = shots + it.shot;
         if (it.kind == 0) {
             const TileArgs a = sd->a;
+            if (!smem_fits<M, P>(rows_max, src_cap, a.n0, status)) return;
             const float *src_row = nullptr;
             int s0 = 0, nsrc = 0;
             if (sd->src) {
@@ -131,8 +134,7 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    const size_t smem = tma_smem_core(M, stages, rows_max) + sizeof(SrcEntry) * (size_t)src_cap +
-                        sizeof(int) * (size_t)(n0_max + 1);
+    const size_t smem = tma_smem_bytes(M, stages, rows_max, n0_max, src_cap);
     if (smem > (size_t)smem_max) return set_error(FD_ERR_UNSUPPORTED, "batch: %d stages do not fit", stages);
     const int threads = 16 * rows_max;
     int occ = std::min((int)((size_t)smem_sm / (smem + 1024)), 2048 / threads);

@@ -92,20 +92,36 @@ __host__ __device__ constexpr int round_up32(int x) { return (x + 31) / 32 * 32;
 // floats of one ring plane (rounded so every plane starts 128-byte aligned)
 __host__ __device__ inline int ring_plane_floats(int box_h) { return round_up32(box_h * kBoxW); }
 
-// Shared memory of the tiled kernel: the u^n ring, the aux ring, the
-// mbarriers and the abort flag; then room for src_cap injected corners of the
-// tile and their per-plane starts.
-__host__ __device__ inline size_t tma_smem_core(int M, int P, int rows_max)
+// Byte offsets of the areas of a tiled CTA's dynamic shared memory: the u^n
+// ring, the aux ring, the mbarriers, the abort flag (16 bytes), then src_cap
+// injected corners of the tile and their n0 + 1 per-plane starts.  Both the
+// size a launch requests and the carve in the kernel come from here.
+struct SmemLayout {
+    size_t aux, bars, abort, src, sstart, end;
+};
+
+__host__ __device__ inline SmemLayout tma_smem_layout(int M, int P, int rows_max, int src_cap, int n0)
 {
     const int NU = M + 1 + P, NA = P + 1;
-    const int box_h = rows_max + 2 * M;
-    return sizeof(float) * ((size_t)NU * ring_plane_floats(box_h) + (size_t)NA * 3 * rows_max * kTileW) +
-           sizeof(unsigned long long) * (NU + NA) + 16;
+    SmemLayout l;
+    l.aux = sizeof(float) * (size_t)NU * ring_plane_floats(rows_max + 2 * M);
+    l.bars = l.aux + sizeof(float) * (size_t)NA * 3 * rows_max * kTileW;
+    l.abort = l.bars + sizeof(unsigned long long) * (size_t)(NU + NA);
+    l.src = l.abort + 16;
+    l.sstart = l.src + sizeof(SrcEntry) * (size_t)src_cap;
+    l.end = l.sstart + sizeof(int) * (size_t)(n0 + 1);
+    return l;
+}
+
+// Without the point lists (the part every launch needs).
+__host__ __device__ inline size_t tma_smem_core(int M, int P, int rows_max)
+{
+    return tma_smem_layout(M, P, rows_max, 0, 0).src;
 }
 
 __host__ __device__ inline size_t tma_smem_bytes(int M, int P, int rows_max, int n0, int src_cap)
 {
-    return tma_smem_core(M, P, rows_max) + sizeof(SrcEntry) * (size_t)src_cap + sizeof(int) * (size_t)(n0 + 1);
+    return tma_smem_layout(M, P, rows_max, src_cap, n0).end;
 }
 
 
@@ -120,21 +136,39 @@ struct SweepSmem {
     int plane_u, plane_a;
 };
 
+__device__ __forceinline__ uint32_t dynamic_smem_bytes()
+{
+    uint32_t v;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+// True when the launch's dynamic shared memory holds the layout of a CTA with
+// these parameters; otherwise records FD_ERR_LAYOUT in the status word (the
+// CTA must then return without touching shared memory).
+template <int M, int P>
+__device__ inline bool smem_fits(int rows_max, int src_cap, int n0, int *status)
+{
+    if (tma_smem_layout(M, P, rows_max, src_cap, n0).end <= (size_t)dynamic_smem_bytes()) return true;
+    if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
+    return false;
+}
+
 // Carve the dynamic shared memory of a CTA whose columns have at most
 // rows_max rows, n0_max planes and src_cap injected corners.
 template <int M, int P>
 __device__ inline SweepSmem carve_smem(unsigned char *raw, int rows_max, int src_cap)
 {
-    constexpr int NU = M + 1 + P, NA = P + 1;
+    const SmemLayout l = tma_smem_layout(M, P, rows_max, src_cap, 0);
     SweepSmem sm;
     sm.plane_u = ring_plane_floats(rows_max + 2 * M);
     sm.plane_a = rows_max * kTileW;
     sm.ring = reinterpret_cast<float *>(raw);
-    sm.aux = sm.ring + NU * sm.plane_u;
-    sm.bars = reinterpret_cast<unsigned long long *>(sm.aux + NA * 3 * sm.plane_a);
-    sm.abort = reinterpret_cast<volatile int *>(sm.bars + NU + NA);
-    sm.src = reinterpret_cast<SrcEntry *>(sm.bars + NU + NA) + 1;
-    sm.sstart = reinterpret_cast<int *>(sm.src + src_cap);
+    sm.aux = reinterpret_cast<float *>(raw + l.aux);
+    sm.bars = reinterpret_cast<unsigned long long *>(raw + l.bars);
+    sm.abort = reinterpret_cast<volatile int *>(raw + l.abort);
+    sm.src = reinterpret_cast<SrcEntry *>(raw + l.src);
+    sm.sstart = reinterpret_cast<int *>(raw + l.sstart);
     return sm;
 }
 

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
     // an earlier launch of this operator gave up on a wait: do nothing until
     // the host has read and cleared the status word
     if (*reinterpret_cast<volatile int *>(status) != 0) return;
+    if (!smem_fits<M, P>(a.rows_max, src_cap, a.n0, status)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SweepSmem sm = carve_smem<M, P>(smem_raw, a.rows_max, src_cap);
     if (threadIdx.x == 0) {
