@@ -9,7 +9,7 @@ the device at most.
   acoustic   the tiled grid update (512^3 SO8 by default)
   batch      the batched-shots persistent kernel (8 windows of the 512^3 model)
   gradient   forward, checkpoint recomputation, adjoint and imaging of one
-             shot (256^3 SO8, 100 steps)
+             shot (256^3 SO8, 100 steps, checkpoints every 10 steps)
   diffusion  the 2D diffusion cluster kernel (256^2 ring, 500 steps per run)
   conv       the closure network's forward convolutions (160^3 activations)
   wgrad      the closure network's weight-gradient kernel (96^3)
@@ -73,7 +73,7 @@ def case_gradient(args):
     cfg = wl.gradient_config(n=args.n, nt=args.nt)
     prop = Propagator(cfg["shape"], cfg["spacing"], cfg["origin"], 8,
                       Shot(cfg["shots"][0], cfg["wavelet"], cfg["rec_coords"]), args.nt, cfg["dt"],
-                      checkpoint_every=min(50, args.nt))
+                      checkpoint_every=min(10, args.nt))
     prop.set_damping(cfg["eta"])
     prop.set_model(torch.from_numpy(cfg["m_true"]).cuda())
     d_obs = prop.forward().clone()
