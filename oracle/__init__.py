@@ -218,6 +218,37 @@ def diffusion(u0, spacing, space_order, a, dt, nt, precision="f64"):
     return u
 
 
+def convection(u0, spacing, c, dt, nt, precision="f64"):
+    """Linear convection (Eq. 2dconvdiscr), nt upwind steps on a 2D grid with
+    the zero halo; returns u^nt."""
+    dt_, ct = _real(precision)
+    u = np.array(u0, dtype=dt_, copy=True)
+    assert u.ndim == 2
+    shp = np.array(u.shape, dtype=np.int64)
+    spc = np.array(spacing, dtype=np.float64)
+    fn = getattr(_lib(), "or_convection_" + precision)
+    _check(fn(_p(shp, ctypes.c_int64), _p(spc, ctypes.c_double), ctypes.c_double(c), ctypes.c_double(dt),
+              ctypes.c_int64(nt), _p(u, ct)), "convection")
+    return u
+
+
+def laplace(p0, spacing, tol, max_iter, precision="f64"):
+    """Jacobi sweeps of the Laplace example (Eq. 2dlaplace_discr with its
+    Dirichlet rows and Neumann columns); with tol > 0 until the L1 criterion
+    r < tol.  Returns (p, sweeps done, last r)."""
+    dt_, ct = _real(precision)
+    p = np.array(p0, dtype=dt_, copy=True)
+    assert p.ndim == 2
+    shp = np.array(p.shape, dtype=np.int64)
+    spc = np.array(spacing, dtype=np.float64)
+    it = ctypes.c_int64(0)
+    r = ctypes.c_double(0.0)
+    fn = getattr(_lib(), "or_laplace_" + precision)
+    _check(fn(_p(shp, ctypes.c_int64), _p(spc, ctypes.c_double), ctypes.c_double(tol), ctypes.c_int64(max_iter),
+              _p(p, ct), ctypes.byref(it), ctypes.byref(r)), "laplace")
+    return p, int(it.value), float(r.value)
+
+
 def step_points(shape, spacing, space_order, m, eta, dt, u_cur32, u_prev32, flat_idx):
     """One forward update (no injection) in FP64 at flat indices, from FP32 states."""
     ndim, shp, spc, _ = _grid_args(shape, spacing)

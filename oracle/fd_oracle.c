@@ -33,6 +33,11 @@
  *   or_acoustic_gradient_f64  objective 1/2 |R u - d|^2 and its adjoint-state
  *                           gradient with respect to m (the adjoint of the
  *                           Seismic Inversion Example used for inversion)
+ *   or_convection_*         Linear Convection section: Eq. 2dconvdiscr
+ *                           (forward Euler, backward differences)
+ *   or_laplace_*            Laplace equation section: Eq. 2dlaplace_discr
+ *                           Jacobi sweeps with the Dirichlet and Neumann
+ *                           boundary expressions and the L1 stopping rule
  */
 #include <math.h>
 #include <stdint.h>

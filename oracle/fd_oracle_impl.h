@@ -267,6 +267,92 @@ int FN(or_interpolate)(int ndim, const int64_t *shape, const double *spacing,
     return 0;
 }
 
+
+/* Linear convection (Linear Convection section, Eq. 2dconvdiscr): forward
+ * Euler in time and backward first differences in space,
+ *   u+(i,j) = u(i,j) - c dt D_x u - c dt D_y u,
+ * D_a u = (w_0 u(i-1) + w_1 u(i)) / h_a with (w_0, w_1) = or_weights(1, {-1, 0}),
+ * on every node of a 2D grid (x = the first axis), zero outside (zero halo).
+ * nt steps in place. */
+int FN(or_convection)(const int64_t *shape, const double *spacing, double c, double dt, int64_t nt, REAL *u)
+{
+    const int64_t nx = shape[0], ny = shape[1];
+    if (nx < 1 || ny < 1) return -1;
+    double off[2] = {-1.0, 0.0}, w[2];
+    if (or_weights(1, 2, off, w) != 0) return -1;
+    const REAL ax = (REAL)(c * dt / spacing[0]), ay = (REAL)(c * dt / spacing[1]);
+    const REAL w0 = (REAL)w[0], w1 = (REAL)w[1];
+    REAL *v = (REAL *)malloc(sizeof(REAL) * nx * ny);
+    if (!v) return -2;
+    for (int64_t s = 0; s < nt; s++) {
+        for (int64_t i = 0; i < nx; i++)
+            for (int64_t j = 0; j < ny; j++) {
+                const REAL uc = u[i * ny + j];
+                const REAL ux = i > 0 ? u[(i - 1) * ny + j] : (REAL)0;
+                const REAL uy = j > 0 ? u[i * ny + j - 1] : (REAL)0;
+                v[i * ny + j] = uc - ax * (w0 * ux + w1 * uc) - ay * (w0 * uy + w1 * uc);
+            }
+        memcpy(u, v, sizeof(REAL) * nx * ny);
+    }
+    free(v);
+    return 0;
+}
+
+/* Laplace equation section (Eq. 2dlaplace_discr): Jacobi sweeps of the
+ * central second differences solved for the centre,
+ *   p+(i,j) = (dy^2 (p(i+1,j) + p(i-1,j)) + dx^2 (p(i,j+1) + p(i,j-1))) / (2 (dx^2 + dy^2))
+ * on the interior nodes (weights from or_weights_central2(2)), followed by the
+ * boundary expressions in the order the paper's operator lists them: the
+ * x = 0 and x = max rows keep their given values (Dirichlet: p = 0 and
+ * p = bc_right), then p+(:,0) = p+(:,1) and p+(:,ny-1) = p+(:,ny-2)
+ * (Neumann, including the corners).  With tol > 0 the sweeps stop once
+ * r = |sum|p+| - sum|p|| / sum|p| < tol (sums in FP64; r = inf while sum|p|
+ * = 0), at most max_iter sweeps; with tol <= 0 exactly max_iter sweeps.
+ * *iters = sweeps done, *r_last = r of the last sweep. */
+int FN(or_laplace)(const int64_t *shape, const double *spacing, double tol, int64_t max_iter, REAL *p,
+                   int64_t *iters, double *r_last)
+{
+    const int64_t nx = shape[0], ny = shape[1];
+    if (nx < 3 || ny < 3) return -1;
+    double w2[2];
+    if (or_weights_central2(2, w2) != 0) return -1;
+    /* central second difference: (w1 p(-1) + w0 p(0) + w1 p(+1)) / h^2 = 0 solved for p(0) */
+    const double hx2 = spacing[0] * spacing[0], hy2 = spacing[1] * spacing[1];
+    const double den = -w2[0] * (1.0 / hx2 + 1.0 / hy2);
+    const REAL wx = (REAL)(w2[1] / hx2 / den), wy = (REAL)(w2[1] / hy2 / den);
+    REAL *v = (REAL *)malloc(sizeof(REAL) * nx * ny);
+    if (!v) return -2;
+    double s_old = 0.0;
+    for (int64_t k = 0; k < nx * ny; k++) s_old += fabs((double)p[k]);
+    int64_t it = 0;
+    double r = INFINITY;
+    while (it < max_iter) {
+        for (int64_t i = 1; i < nx - 1; i++)
+            for (int64_t j = 1; j < ny - 1; j++)
+                v[i * ny + j] = wx * (p[(i + 1) * ny + j] + p[(i - 1) * ny + j]) +
+                                wy * (p[i * ny + j + 1] + p[i * ny + j - 1]);
+        for (int64_t j = 0; j < ny; j++) {
+            v[j] = p[j];
+            v[(nx - 1) * ny + j] = p[(nx - 1) * ny + j];
+        }
+        for (int64_t i = 0; i < nx; i++) {
+            v[i * ny] = v[i * ny + 1];
+            v[i * ny + ny - 1] = v[i * ny + ny - 2];
+        }
+        memcpy(p, v, sizeof(REAL) * nx * ny);
+        it++;
+        double s_new = 0.0;
+        for (int64_t k = 0; k < nx * ny; k++) s_new += fabs((double)p[k]);
+        r = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
+        s_old = s_new;
+        if (tol > 0.0 && r < tol) break;
+    }
+    free(v);
+    if (iters) *iters = it;
+    if (r_last) *r_last = r;
+    return 0;
+}
+
 #undef FN
 #undef CAT
 #undef CAT2
