@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    p.add_argument("--rows", default="diffusion,gradient,batched,learned",
+    p.add_argument("--rows", default="diffusion,convection,laplace,gradient,batched,learned",
                    help="secondary rows to run (comma-separated)")
     p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
     p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel (default: autotuned)")
@@ -243,10 +243,90 @@ def bench_diffusion(steps=5, warmup=3):
     op.sync()
     ms = e0.elapsed_time(e1) / steps
     pts = float(cfg["shape"][0] * cfg["shape"][1]) * cfg["nt"]
+    k, ctas = fd.fd_operator_get_time_block(op.handle)
     return {"workload": "diffusion2d_256^2_ring_so2_nt500", "value": pts / (ms * 1e-3) / 1e9, "unit": "GPts/s",
             "ms_per_run": ms, "us_per_time_step": 1e3 * ms / cfg["nt"],
-            "launches_per_run": (op.launches - n0) / steps,
+            "launches_per_run": (op.launches - n0) / steps, "cluster_ctas": ctas, "steps_per_exchange": k,
             "bound": "latency (grid held in one cluster's shared memory)"}
+
+
+def _time_runs(fn, reps, warmup=3):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_convection(reps=20):
+    """The Linear Convection example (81^2, c = 1, 100 upwind steps): one
+    cluster launch per run; against the plain per-step kernels."""
+    import torch
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    cfg = wl.convection_config()
+    grid = fd.Grid(cfg["shape"], cfg["spacing"])
+    u = fd.TimeData("u", grid)
+    u0 = torch.from_numpy(cfg["u0"]).cuda()
+    out = {}
+    for name, flags in (("cluster", 0), ("plain", fd.FD_FLAG_PLAIN_KERNELS)):
+        op = fd.Operator(fd.FD_CONVECTION_UPWIND, 1, u, a=cfg["c"], flags=flags)
+
+        def run():
+            u.at(0).copy_(u0)
+            op.apply(0, cfg["nt"], cfg["dt"])
+
+        out[name] = _time_runs(run, reps)
+        if name == "cluster":
+            k, ctas = fd.fd_operator_get_time_block(op.handle)
+        op.sync()
+    pts = float(cfg["shape"][0] * cfg["shape"][1]) * cfg["nt"]
+    return {"workload": "convection2d_81^2_c1_nt100", "value": pts / (out["cluster"] * 1e-3) / 1e9,
+            "unit": "GPts/s", "ms_per_run": out["cluster"], "us_per_time_step": 1e3 * out["cluster"] / cfg["nt"],
+            "plain_ms_per_run": out["plain"], "speedup_vs_plain": out["plain"] / out["cluster"],
+            "cluster_ctas": ctas, "steps_per_exchange": k}
+
+
+def bench_laplace(reps=5):
+    """The Laplace example (31^2 on [0,2]x[0,1], Dirichlet rows, Neumann
+    columns) to the L1 criterion 1e-4: the whole convergence loop in one
+    cluster launch that decides on the device; against per-sweep launches
+    with the sum read back every sweep."""
+    import torch
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    cfg = wl.laplace_config()
+    grid = fd.Grid(cfg["shape"], cfg["spacing"])
+    u = fd.TimeData("u", grid)
+    p0 = torch.from_numpy(cfg["p0"]).cuda()
+    out = {}
+    for name, flags in (("cluster", 0), ("plain", fd.FD_FLAG_PLAIN_KERNELS)):
+        op = fd.Operator(fd.FD_LAPLACE_JACOBI, 2, u, flags=flags)
+        res = []
+
+        def run():
+            u.at(0).copy_(p0)
+            res.append(op.converge(0, 1000000, cfg["tol"]))
+
+        run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            run()
+        out[name] = ((time.perf_counter() - t0) / reps * 1e3, res[-1])
+    it = out["cluster"][1][0]
+    return {"workload": "laplace2d_31^2_tol1e-4", "unit": "ms to convergence", "value": out["cluster"][0],
+            "sweeps": it, "r_last": out["cluster"][1][1], "us_per_sweep": 1e3 * out["cluster"][0] / it,
+            "plain_ms": out["plain"][0], "plain_sweeps": out["plain"][1][0],
+            "speedup_vs_plain": out["plain"][0] / out["cluster"][0]}
 
 
 def bench_gradient(n=256, nt=1500, k=50, shots=1):
@@ -578,8 +658,8 @@ def run_ours(args):
 
     rows = None
     if rank == 0 and not args.no_rows:
-        fns = {"diffusion": bench_diffusion, "gradient": bench_gradient, "batched": bench_batched,
-               "learned": bench_learned}
+        fns = {"diffusion": bench_diffusion, "convection": bench_convection, "laplace": bench_laplace,
+               "gradient": bench_gradient, "batched": bench_batched, "learned": bench_learned}
         rows = {name: fns[name]() for name in args.rows.split(",") if name in fns}
 
     if rank == 0:

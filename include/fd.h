@@ -184,7 +184,26 @@ enum {
      * with c = dt^2/m and d = dt*eta/m evaluated at each node.  u: 2 slots,
      * slot n%2 holds u^n; step n overwrites slot (n+1)%2 (u^{n-1}) with
      * u^{n+1}.  Needs m; eta, src, rec optional. */
-    FD_ACOUSTIC_LEAPFROG = 2
+    FD_ACOUSTIC_LEAPFROG = 2,
+    /* u_t + c u_x + c u_y = 0 (Linear Convection section, Eq. 2dconvdiscr):
+     *   u^{n+1} = u^n - (c dt/dx)(u^n - u^n[i-1,j]) - (c dt/dy)(u^n - u^n[i,j-1])
+     * forward Euler with backward (upwind) differences, on every node of a 2D
+     * grid (x = the first axis), zero halo.  space_order must be 1; `a` is the
+     * velocity c > 0.  u: 2 slots, ping-pong as diffusion.  Stable (and
+     * monotone) for c dt (1/dx + 1/dy) <= 1, which apply checks. */
+    FD_CONVECTION_UPWIND = 3,
+    /* p_xx + p_yy = 0 (Laplace equation section, Eq. 2dlaplace_discr): one
+     * Jacobi sweep per step n,
+     *   p^{n+1}[i,j] = (dy^2 (p[i+1,j] + p[i-1,j]) + dx^2 (p[i,j+1] + p[i,j-1]))
+     *                  / (2 (dx^2 + dy^2))
+     * on the interior nodes of a 2D grid, followed by the boundary expressions
+     * in the paper's order: the first and last rows (x = 0 and x = max) keep
+     * their values (Dirichlet: the caller stores p = 0 and p = bc_right
+     * there), then the first and last columns copy the next column inwards
+     * (Neumann dp/dy = 0, corners included).  space_order must be 2; dt and
+     * `a` are unused.  u: 2 slots, ping-pong.  See fd_operator_converge for
+     * the paper's convergence loop. */
+    FD_LAPLACE_JACOBI = 4
 };
 
 enum {
@@ -204,12 +223,12 @@ enum {
 };
 
 typedef struct {
-    int kind;              /* FD_DIFFUSION_EULER or FD_ACOUSTIC_LEAPFROG */
-    int space_order;       /* even, 2..16 */
+    int kind;              /* FD_DIFFUSION_EULER, FD_ACOUSTIC_LEAPFROG, FD_CONVECTION_UPWIND, FD_LAPLACE_JACOBI */
+    int space_order;       /* even, 2..16 (convection: 1, Laplace: 2) */
     fd_field *u;           /* 2-slot time field */
     fd_field *m;           /* 1-slot square slowness (acoustic) */
     fd_field *eta;         /* 1-slot damping (acoustic, may be NULL) */
-    double a;              /* diffusivity (diffusion) */
+    double a;              /* diffusivity (diffusion), velocity c (convection) */
     fd_sparse *src;        /* injected points (acoustic, may be NULL) */
     fd_sparse *rec;        /* interpolated points (acoustic, may be NULL) */
     void *cuda_stream;     /* cudaStream_t all work is enqueued on */
@@ -239,6 +258,28 @@ fd_status fd_operator_bind(fd_operator *op, const char *name, void *obj);
  * min m), the undamped leapfrog limit; diffusion: a dt above the explicit
  * Euler limit 2 / (a max lambda)), FD_ERR_CUDA. */
 fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt);
+
+/* The Laplace example's convergence loop (FD_LAPLACE_JACOBI only): Jacobi
+ * sweeps from slot t0%2 until r = |S^{n+1} - S^n| / S^n < tol, with S the sum
+ * of |p| over the grid in FP64 (r is infinite while S^n = 0), or max_iter
+ * sweeps.  The result is in slot (t0 + *iters) % 2.  Small grids run the
+ * whole loop in one cluster launch that decides on the device; larger ones
+ * read S back after every sweep.  Waits for the result.  *iters and *r_last
+ * (may be NULL) receive the sweeps done and the last r.
+ * Errors: FD_ERR_INVALID_ARG (tol <= 0, max_iter < 0), FD_ERR_UNSUPPORTED
+ * (other kinds), FD_ERR_CUDA. */
+fd_status fd_operator_converge(fd_operator *op, int64_t t0, int64_t max_iter, double tol, int64_t *iters,
+                               double *r_last);
+
+/* Steps between halo exchanges (temporal blocking) of the whole-run cluster
+ * kernels of small 2D grids (diffusion, convection, Laplace): k > 0 forces
+ * it, 0 restores the planner's choice.  Results do not depend on k.
+ * Errors: FD_ERR_UNSUPPORTED when the operator has no cluster path or the
+ * strips are thinner than k * half-width rows (the previous value is kept). */
+fd_status fd_operator_set_time_block(fd_operator *op, int k);
+/* The cluster path in use: steps per exchange and CTAs in the cluster (both 0
+ * when the operator runs per-step kernels). */
+fd_status fd_operator_get_time_block(const fd_operator *op, int *k, int *ctas);
 
 /* Wait for the operator's stream and report any deferred device error:
  * FD_ERR_CUDA for a failed launch or kernel, FD_ERR_TIMEOUT when a kernel's

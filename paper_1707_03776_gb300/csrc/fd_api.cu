@@ -52,9 +52,10 @@ struct fd_operator {
     double m_min;          // min(m) over the grid
     int64_t launches;
     fdgb::TmaPlan tma;     // tiled-kernel plan (tensor maps, tiling)
-    bool cluster_ok;       // diffusion: whole run in one cluster launch
-    int cluster_n;
-    size_t cluster_smem;
+    fdgb::ClusterPlan cluster;  // small 2D grids: whole run in one cluster launch
+    int want_k;            // forced steps per cluster exchange (0: planner)
+    float jac_wr, jac_wc;  // Laplace: weights of the row and column neighbours
+    void *conv_res;        // Laplace: device {int64 steps, double r, double sum}
     // stencil-kernel timing (fd_operator_profile)
     std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
     int64_t prof_max;
@@ -446,9 +447,27 @@ static cudaError_t profile_mark(fd_operator *op, int which)
     return r;
 }
 
+// The whole-run cluster plan of a 2D diffusion, convection or Laplace
+// operator (none for other kinds or grids that do not fit).
+static void plan_cluster(fd_operator *op)
+{
+    op->cluster = ClusterPlan();
+    int rule = -1, M = 1;
+    if (op->kind == FD_DIFFUSION_EULER) {
+        rule = kRuleDiffusion;
+        M = op->so / 2;
+    } else if (op->kind == FD_CONVECTION_UPWIND) {
+        rule = kRuleUpwind;
+    } else if (op->kind == FD_LAPLACE_JACOBI) {
+        rule = kRuleJacobi;
+    }
+    if (rule >= 0) cluster_plan_build(rule, M, op->geom, op->want_k, &op->cluster);
+}
+
 static void release(fd_operator *op)
 {
     if (!op) return;
+    if (op->conv_res) cudaFreeAsync(op->conv_res, op->stream);
     profile_clear(op);
     if (op->c) cudaFreeAsync(op->c, op->stream);
     if (op->d) cudaFreeAsync(op->d, op->stream);
@@ -461,13 +480,24 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
 {
     if (!desc || !out) return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: null pointer");
     *out = nullptr;
-    if (desc->kind != FD_DIFFUSION_EULER && desc->kind != FD_ACOUSTIC_LEAPFROG)
-        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: unknown kind %d", desc->kind);
-    if (desc->space_order < 2 || desc->space_order > 16 || desc->space_order % 2)
+    const int kind = desc->kind;
+    if (kind != FD_DIFFUSION_EULER && kind != FD_ACOUSTIC_LEAPFROG && kind != FD_CONVECTION_UPWIND &&
+        kind != FD_LAPLACE_JACOBI)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: unknown kind %d", kind);
+    if (kind == FD_CONVECTION_UPWIND && desc->space_order != 1)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: convection is first order (space_order 1)");
+    if (kind == FD_LAPLACE_JACOBI && desc->space_order != 2)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: the Laplace sweep is second order (space_order 2)");
+    if (kind != FD_CONVECTION_UPWIND &&
+        (desc->space_order < 2 || desc->space_order > 16 || desc->space_order % 2))
         return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: space order must be even, 2..16");
     if (!desc->u || desc->u->levels != 2)
         return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: u must be a 2-slot field");
     const fd_grid &g = desc->u->g;
+    if ((kind == FD_CONVECTION_UPWIND || kind == FD_LAPLACE_JACOBI) && g.ndim != 2)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: the convection and Laplace operators are 2D");
+    if (kind == FD_LAPLACE_JACOBI && (g.shape[0] < 3 || g.shape[1] < 3))
+        return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: the Laplace sweep needs at least 3 x 3 nodes");
     if (desc->kind == FD_ACOUSTIC_LEAPFROG) {
         if (!desc->m || desc->m->levels != 1 || !same_shape(desc->m->g, g))
             return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: acoustic needs a 1-slot m of u's shape");
@@ -476,10 +506,11 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
         if ((desc->src && !same_shape(desc->src->g, g)) || (desc->rec && !same_shape(desc->rec->g, g)))
             return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: sparse grid differs from u's");
     } else {
-        if (!(desc->a > 0.0) || !std::isfinite(desc->a))
-            return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: diffusivity a must be > 0");
+        if (kind != FD_LAPLACE_JACOBI && (!(desc->a > 0.0) || !std::isfinite(desc->a)))
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_create: %s must be > 0",
+                             kind == FD_CONVECTION_UPWIND ? "velocity c (a)" : "diffusivity a");
         if (desc->flags & FD_FLAG_REVERSE)
-            return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: diffusion has no reverse mode");
+            return set_error(FD_ERR_UNSUPPORTED, "fd_operator_create: only the acoustic operator has a reverse mode");
     }
     fd_operator *op = new (std::nothrow) fd_operator();
     if (!op) return set_error(FD_ERR_NOMEM, "fd_operator_create: out of host memory");
@@ -501,8 +532,22 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     op->launches = 0;
     op->prof_max = 0;
     op->prof_used = 0;
-    fd_status s = build_coef(op);
+    op->want_k = 0;
+    op->jac_wr = op->jac_wc = 0.0f;
+    op->conv_res = nullptr;
+    std::memset(&op->coef, 0, sizeof op->coef);
+    op->lambda_max = 0.0;
+    fd_status s = op->kind == FD_CONVECTION_UPWIND ? FD_OK : build_coef(op);
     if (s != FD_OK) { release(op); return s; }
+    if (op->kind == FD_LAPLACE_JACOBI) {
+        // central second differences solved for the centre: the row (x)
+        // neighbours weigh dy^2, the column (y) neighbours dx^2, over 2(dx^2+dy^2)
+        const double hx2 = g.spacing[0] * g.spacing[0], hy2 = g.spacing[1] * g.spacing[1];
+        op->jac_wr = (float)(hy2 / (2.0 * (hx2 + hy2)));
+        op->jac_wc = (float)(hx2 / (2.0 * (hx2 + hy2)));
+        cudaError_t e2 = cudaMallocAsync(&op->conv_res, 32, op->stream);
+        if (e2 != cudaSuccess) { release(op); return cuda_error(e2, "fd_operator_create: result word"); }
+    }
     cudaError_t e = cudaMallocAsync((void **)&op->status, sizeof(int), op->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(op->status, 0, sizeof(int), op->stream);
     if (e != cudaSuccess) { release(op); return cuda_error(e, "fd_operator_create: status word"); }
@@ -522,8 +567,7 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     if (s != FD_OK) { release(op); return s; }
     s = rebuild_fused(op);
     if (s != FD_OK) { release(op); return s; }
-    op->cluster_ok = op->kind == FD_DIFFUSION_EULER &&
-                     diffusion_cluster_fits(op->so / 2, op->geom, &op->cluster_n, &op->cluster_smem);
+    plan_cluster(op);
     *out = op;
     return FD_OK;
 }
@@ -582,6 +626,13 @@ static fd_status check_dt(const fd_operator *op, double dt, const char *who)
 {
     if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(FD_ERR_INVALID_ARG, "%s: dt must be > 0", who);
     if (op->flags & FD_FLAG_NO_CFL_CHECK) return FD_OK;
+    if (op->kind == FD_CONVECTION_UPWIND) {
+        const fd_grid &g = op->u->g;
+        const double nu = op->a * dt * (1.0 / g.spacing[0] + 1.0 / g.spacing[1]);
+        if (nu > 1.0)
+            return set_error(FD_ERR_UNSTABLE, "%s: c dt (1/dx + 1/dy) = %g above the upwind limit 1", who, nu);
+        return FD_OK;
+    }
     if (op->kind == FD_ACOUSTIC_LEAPFROG) {
         double limit = 2.0 * std::sqrt(op->m_min / op->lambda_max);
         if (dt > limit) return set_error(FD_ERR_UNSTABLE, "%s: dt = %g above the stability limit %g", who, dt, limit);
@@ -615,7 +666,7 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
         if (sp && sp->npoint > 0 && t0 + nt > sp->nt)
             return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: trace has %lld rows, need %lld",
                              (long long)sp->nt, (long long)(t0 + nt));
-    fd_status cs = check_dt(op, dt, "fd_operator_apply");
+    fd_status cs = op->kind == FD_LAPLACE_JACOBI ? FD_OK : check_dt(op, dt, "fd_operator_apply");
     if (cs != FD_OK) return cs;
     if (nt == 0) return FD_OK;
     const int M = op->so / 2;
@@ -664,33 +715,37 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                 }
             }
         }
-    } else if (op->cluster_ok && !(op->flags & FD_FLAG_PLAIN_KERNELS)) {
-        const float adt = (float)(op->a * dt);
-        int64_t done = 0;
-        while (done < nt) {
-            const int64_t chunk = (nt - done) < (int64_t(1) << 30) ? (nt - done) : (int64_t(1) << 30);
-            const int64_t t = t0 + done;
-            float *u0 = op->u->slot[t & 1];
-            float *last = op->u->slot[(t + chunk) & 1];
-            float *prev = chunk >= 2 ? op->u->slot[(t + chunk - 1) & 1] : nullptr;
-            FD_CUDA(profile_mark(op, 0), "profile");
-            FD_CUDA(launch_diffusion_cluster(M, g, op->coef, adt, u0, last, prev, (int)chunk, op->cluster_n,
-                                             op->cluster_smem, st),
-                    "diffusion cluster run");
-            FD_CUDA(profile_mark(op, 1), "profile");
-            op->launches += 1;
-            done += chunk;
-        }
     } else {
+        // 2D diffusion, convection and Laplace sweeps: the whole run in one
+        // cluster launch when the grid fits, else one launch per step
+        const fd_grid &gr = op->u->g;
         const float adt = (float)(op->a * dt);
-        for (int64_t q = 0; q < nt; q++) {
-            int64_t n = t0 + q;
-            int cur = (int)(n & 1);
+        const float nux = op->kind == FD_CONVECTION_UPWIND ? (float)(op->a * dt / gr.spacing[0]) : 0.0f;
+        const float nuy = op->kind == FD_CONVECTION_UPWIND ? (float)(op->a * dt / gr.spacing[1]) : 0.0f;
+        if (op->cluster.ok && !(op->flags & FD_FLAG_PLAIN_KERNELS)) {
             FD_CUDA(profile_mark(op, 0), "profile");
-            FD_CUDA(launch_diffusion_plain(M, g, op->coef, adt, op->u->slot[cur], op->u->slot[cur ^ 1], st),
-                    "diffusion step");
+            FD_CUDA(launch_cluster_run(op->cluster, g, op->coef, adt, nux, nuy, op->jac_wr, op->jac_wc,
+                                       op->u->slot[t0 & 1], op->u->slot[0], op->u->slot[1], t0, nt, 0.0, nullptr,
+                                       nullptr, st),
+                    "cluster run");
             FD_CUDA(profile_mark(op, 1), "profile");
             op->launches += 1;
+        } else {
+            for (int64_t q = 0; q < nt; q++) {
+                int64_t n = t0 + q;
+                int cur = (int)(n & 1);
+                const float *src = op->u->slot[cur];
+                float *dst = op->u->slot[cur ^ 1];
+                FD_CUDA(profile_mark(op, 0), "profile");
+                if (op->kind == FD_DIFFUSION_EULER)
+                    FD_CUDA(launch_diffusion_plain(M, g, op->coef, adt, src, dst, st), "diffusion step");
+                else if (op->kind == FD_CONVECTION_UPWIND)
+                    FD_CUDA(launch_convection_plain(g, nux, nuy, src, dst, st), "convection step");
+                else
+                    FD_CUDA(launch_jacobi_plain(g, op->jac_wr, op->jac_wc, src, dst, nullptr, st), "Laplace sweep");
+                FD_CUDA(profile_mark(op, 1), "profile");
+                op->launches += 1;
+            }
         }
     }
     return FD_OK;
@@ -909,6 +964,84 @@ extern "C" fd_status fd_operator_autotune(fd_operator *op, int64_t t0, int64_t n
     if (best_rows) *best_rows = br;
     if (best_stages) *best_stages = bs;
     if (best_ms_per_step) *best_ms_per_step = bms;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_converge(fd_operator *op, int64_t t0, int64_t max_iter, double tol,
+                                          int64_t *iters, double *r_last)
+{
+    if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_converge: null operator");
+    if (op->kind != FD_LAPLACE_JACOBI)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_converge: only for the Laplace operator");
+    if (!(tol > 0.0) || max_iter < 0 || t0 < 0)
+        return set_error(FD_ERR_INVALID_ARG, "fd_operator_converge: need tol > 0, max_iter >= 0, t0 >= 0");
+    cudaStream_t st = op->stream;
+    const Geom &g = op->geom;
+    long long steps = 0;
+    double r = INFINITY;
+    if (max_iter > 0 && op->cluster.ok && !(op->flags & FD_FLAG_PLAIN_KERNELS)) {
+        long long *d_steps = (long long *)op->conv_res;
+        double *d_r = (double *)((char *)op->conv_res + 8);
+        FD_CUDA(launch_cluster_run(op->cluster, g, op->coef, 0.0f, 0.0f, 0.0f, op->jac_wr, op->jac_wc,
+                                   op->u->slot[t0 & 1], op->u->slot[0], op->u->slot[1], t0, max_iter, tol, d_steps,
+                                   d_r, st),
+                "cluster convergence run");
+        op->launches += 1;
+        unsigned char host[16];
+        FD_CUDA(cudaMemcpyAsync(host, op->conv_res, 16, cudaMemcpyDeviceToHost, st), "convergence result");
+        FD_CUDA(cudaStreamSynchronize(st), "convergence result");
+        std::memcpy(&steps, host, 8);
+        std::memcpy(&r, host + 8, 8);
+    } else if (max_iter > 0) {
+        // per-sweep launches; S read back after every sweep
+        double *d_sum = (double *)((char *)op->conv_res + 16);
+        double s_old = 0.0, s_new = 0.0;
+        FD_CUDA(cudaMemsetAsync(d_sum, 0, sizeof(double), st), "convergence sum");
+        FD_CUDA(launch_abs_sum(g, op->u->slot[t0 & 1], d_sum, st), "convergence sum");
+        FD_CUDA(cudaMemcpyAsync(&s_old, d_sum, sizeof(double), cudaMemcpyDeviceToHost, st), "convergence sum");
+        FD_CUDA(cudaStreamSynchronize(st), "convergence sum");
+        op->launches += 1;
+        while (steps < max_iter) {
+            const int64_t n = t0 + steps;
+            FD_CUDA(cudaMemsetAsync(d_sum, 0, sizeof(double), st), "convergence sum");
+            FD_CUDA(launch_jacobi_plain(g, op->jac_wr, op->jac_wc, op->u->slot[n & 1], op->u->slot[(n + 1) & 1],
+                                        d_sum, st),
+                    "Laplace sweep");
+            FD_CUDA(cudaMemcpyAsync(&s_new, d_sum, sizeof(double), cudaMemcpyDeviceToHost, st), "convergence sum");
+            FD_CUDA(cudaStreamSynchronize(st), "convergence sum");
+            op->launches += 1;
+            steps++;
+            r = s_old > 0.0 ? std::fabs(s_new - s_old) / s_old : INFINITY;
+            s_old = s_new;
+            if (r < tol) break;
+        }
+    }
+    if (iters) *iters = steps;
+    if (r_last) *r_last = r;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_set_time_block(fd_operator *op, int k)
+{
+    if (!op || k < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_set_time_block: bad arguments");
+    if (!op->cluster.ok) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_set_time_block: no cluster path");
+    const int old = op->want_k;
+    const ClusterPlan keep = op->cluster;
+    op->want_k = k;
+    plan_cluster(op);
+    if (!op->cluster.ok || (k > 0 && op->cluster.nctas > 1 && op->cluster.K != k)) {
+        op->want_k = old;
+        op->cluster = keep;
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_set_time_block: %d steps per exchange do not fit", k);
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_operator_get_time_block(const fd_operator *op, int *k, int *ctas)
+{
+    if (!op || !k || !ctas) return set_error(FD_ERR_INVALID_ARG, "fd_operator_get_time_block: null pointer");
+    *k = op->cluster.ok ? op->cluster.K : 0;
+    *ctas = op->cluster.ok ? op->cluster.nctas : 0;
     return FD_OK;
 }
 

@@ -57,11 +57,37 @@ cudaError_t launch_imaging(const Geom &g, float scale, const float *mu, const fl
 cudaError_t launch_diffusion_plain(int half_width, const Geom &g, const Coef &cf, float adt,
                                    const float *u, float *u_out, cudaStream_t st);
 
-// whole-run diffusion in one thread-block cluster (2D grids that fit in the
-// cluster's shared memory)
-bool diffusion_cluster_fits(int half_width, const Geom &g, int *nclusters, size_t *smem);
-cudaError_t launch_diffusion_cluster(int half_width, const Geom &g, const Coef &cf, float adt,
-                                     const float *u0, float *out_last, float *out_prev, int nt,
-                                     int nclusters, size_t smem, cudaStream_t st);
+// plain 2D kernels of the Linear Convection and Laplace examples
+// upwind: out = u - nux (u - u[i-1,j]) - nuy (u - u[i,j-1]), zero halo
+cudaError_t launch_convection_plain(const Geom &g, float nux, float nuy, const float *u, float *out,
+                                    cudaStream_t st);
+// Jacobi sweep with the Dirichlet rows and Neumann columns; if sum is not
+// null, *sum += sum of |out| (FP64)
+cudaError_t launch_jacobi_plain(const Geom &g, float wr, float wc, const float *p, float *out, double *sum,
+                                cudaStream_t st);
+// sum += sum of |u| over the interior (FP64)
+cudaError_t launch_abs_sum(const Geom &g, const float *u, double *sum, cudaStream_t st);
+
+// Whole runs of small 2D grids in one thread-block cluster (k_cluster.cu)
+enum { kRuleDiffusion = 0, kRuleUpwind = 1, kRuleJacobi = 2 };
+struct ClusterPlan {
+    bool ok = false;
+    int rule = 0;
+    int M = 1;        // stencil half-width
+    int nctas = 0;    // CTAs in the cluster
+    int K = 1;        // steps between halo exchanges
+    int halo = 0;     // halo rows per side
+    size_t smem = 0;  // dynamic shared memory per CTA
+};
+// Plan a rule on a 2D grid; want_k > 0 forces the steps per exchange.
+// Returns false when the grid does not fit in a cluster.
+bool cluster_plan_build(int rule, int half_width, const Geom &g, int want_k, ClusterPlan *out);
+// nt steps from u0 (slot t0 % 2); the last two states go to slot0/slot1 by
+// time parity.  Jacobi with tol > 0 stops on the L1 criterion; res_steps /
+// res_r (device, may be null) receive the steps done and the last r.
+cudaError_t launch_cluster_run(const ClusterPlan &p, const Geom &g, const Coef &cf, float adt, float nux,
+                               float nuy, float wr, float wc, const float *u0, float *slot0, float *slot1,
+                               long long t0, long long nt, double tol, long long *res_steps, double *res_r,
+                               cudaStream_t st);
 
 }  // namespace fdgb

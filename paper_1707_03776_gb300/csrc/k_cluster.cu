@@ -1,17 +1,39 @@
-// Explicit diffusion on small 2D grids: the whole time loop in one launch of
-// one thread-block cluster.
+// Small 2D grids: the whole time loop (or convergence loop) in one launch of
+// one thread-block cluster, with K steps between halo exchanges.
 //
-// A 2D grid that fits in the shared memory of a cluster (the 254^2 interior of
-// the 256^2 ring workload needs 2 x 34 x 264 floats per CTA with 8 CTAs) is
-// split into row strips, one per CTA.  Each CTA keeps its strip plus M halo
-// rows above and below, twice (ping-pong), in shared memory.  Per step every
-// thread updates its points from one buffer into the other and, for the M
-// first and last rows of the strip, also writes the new values into the
-// neighbouring CTAs' halo rows through distributed shared memory; one cluster
-// barrier then separates the steps.  Grid data touches global memory only at
-// the start (u^{t0}) and at the end (the last two states, so that the slot
-// convention of per-step launches holds: slot n%2 holds u^n).
+// The grid's rows are split into strips, one per CTA.  Each CTA keeps its
+// strip plus H = K*M halo rows above and below, twice (ping-pong), in shared
+// memory.  A block of K steps runs without any inter-CTA communication: step
+// j of the block also updates the (K-1-j)*M halo rows nearest the strip
+// (redundantly with the neighbour, same arithmetic), so the rows the next step
+// reads are always current.  After the block every CTA writes its first and
+// last H rows into its neighbours' inboxes through distributed shared memory,
+// one cluster barrier separates the writes from the reads, and each CTA copies
+// its inbox into its halo rows.  Inboxes alternate between two buffers by
+// block parity, so one barrier per block is enough (a neighbour can only write
+// the same inbox again after the next barrier, which this CTA reaches after
+// reading it).  Temporal blocking trades (K-1)*M redundant rows per strip for
+// K-times fewer cluster barriers.
+//
+// Update rules (the operator kinds of the 2D examples):
+//   diffusion  u+ = u + a dt L u            (SO 2..16, zero halo)
+//   upwind     u+ = u - nu_x (u - u[i-1,j]) - nu_y (u - u[i,j-1])
+//              (Linear Convection, Eq. 2dconvdiscr; zero halo)
+//   jacobi     Laplace equation, Eq. 2dlaplace_discr, on interior nodes; the
+//              first and last rows keep their values (Dirichlet), then the
+//              first and last columns copy their neighbour column (Neumann,
+//              corners included) -- in the order the paper lists them.
+// The jacobi rule can stop on the L1 criterion r = |S+ - S| / S < tol, with S
+// the grid's sum of |p| in FP64: every CTA adds its rows' partial sum to a
+// slot of its shared memory, and after the barrier every CTA reads all slots
+// in rank order, so all take the same decision.
+//
+// Grid data touches global memory only at the start (u^{t0}) and at the end:
+// the last state goes to slot (t0+steps)%2 and the one before it to the other
+// slot, which keeps the convention of per-step launches (slot n%2 holds u^n).
 #include <cooperative_groups.h>
+
+#include <algorithm>
 
 #include "fd_internal.h"
 #include "fd_internal_host.h"
@@ -22,156 +44,372 @@ namespace fdgb {
 
 namespace {
 
-constexpr int kClusterThreads = 512;
+constexpr int kCThreads = 512;
 
 struct ClusterArgs {
-    int rows;         // grid rows (axis d1 of the 3-axis view)
-    int cols;         // grid columns (contiguous axis)
+    int rows, cols;   // grid rows (axis d1) and columns (contiguous axis d2)
     long long s1;     // row stride in global memory (elements)
     int strip;        // rows per CTA at most
-    int width;        // shared row pitch: cols + 2M, rounded to 4
-    int nclusters;    // CTAs in the cluster
+    int width;        // shared row pitch: cols + 2 hc, rounded to 4
+    int hc;           // zero columns on each side
+    int halo;         // halo rows on each side: K*M (M when alone)
+    int K;            // steps between exchanges
+    int nctas;        // CTAs in the cluster
+    int tc, tr;       // threads along columns and rows
 };
 
-template <int M>
-__global__ void __launch_bounds__(kClusterThreads, 1)
-    diffusion_cluster_kernel(const ClusterArgs a, const Coef cf, float adt, const float *__restrict__ u0,
-                             float *__restrict__ out_last, float *__restrict__ out_prev, int nt)
+struct RuleArgs {
+    Coef cf;
+    float adt;        // diffusion: a dt
+    float nux, nuy;   // upwind: c dt / h per axis
+    float wr, wc;     // jacobi: weights of the row and column neighbours
+};
+
+template <int RULE, int M>
+__device__ __forceinline__ float apply_rule(const float *__restrict__ src, int at, int W, int gr, int c,
+                                            const ClusterArgs &a, const RuleArgs &ra)
 {
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    extern __shared__ __align__(16) float sbuf[];
-    const int W = a.width;
-    const int H = a.strip + 2 * M;  // rows held: halo + strip + halo
-    float *const buf0 = sbuf;
-    float *const buf1 = sbuf + H * W;
-
-    const int r0 = (int)((long long)rank * a.rows / a.nclusters);
-    const int r1 = (int)((long long)(rank + 1) * a.rows / a.nclusters);
-    const int nr = r1 - r0;
-    const int tid = threadIdx.x;
-
-    // load rows r0-M .. r1+M-1 (zero outside the grid) and zero the side halos
-    for (int q = tid; q < 2 * H * W; q += blockDim.x) {
-        const int b = q / (H * W);
-        const int rem = q - b * H * W;
-        const int lr = rem / W;
-        const int c = rem - lr * W - M;
-        const int gr = r0 - M + lr;
-        float v = 0.0f;
-        if (b == 0 && c >= 0 && c < a.cols && gr >= 0 && gr < a.rows && lr < nr + 2 * M)
-            v = u0[(long long)gr * a.s1 + c];
-        (b == 0 ? buf0 : buf1)[rem] = v;
-    }
-    cluster.sync();
-
-    float *up_nb = nullptr;  // neighbour above (rank-1): its bottom halo rows
-    float *dn_nb = nullptr;  // neighbour below (rank+1): its top halo rows
-    const int npts = nr * a.cols;
-    for (int step = 0; step < nt; step++) {
-        const float *src = (step & 1) ? buf1 : buf0;
-        float *dst = (step & 1) ? buf0 : buf1;
-        if (rank > 0) up_nb = cluster.map_shared_rank(dst, rank - 1);
-        if (rank + 1 < a.nclusters) dn_nb = cluster.map_shared_rank(dst, rank + 1);
-        for (int p = tid; p < npts; p += blockDim.x) {
-            const int lr = p / a.cols;
-            const int c = p - lr * a.cols;
-            const int at = (lr + M) * W + c + M;
-            float lap = cf.centre * src[at];
+    if (RULE == kRuleDiffusion) {
+        const float u = src[at];
+        float lap = ra.cf.centre * u;
 #pragma unroll
-            for (int k = 1; k <= M; k++) {
-                lap = fmaf(cf.ax[2][k], src[at - k] + src[at + k], lap);
-                lap = fmaf(cf.ax[1][k], src[at - k * W] + src[at + k * W], lap);
-            }
-            const float v = fmaf(adt, lap, src[at]);
-            dst[at] = v;
-            // the neighbour above holds our first M rows as its last M halo rows
-            if (lr < M && up_nb) {
-                const int nb_nr = r0 - (int)((long long)(rank - 1) * a.rows / a.nclusters);
-                up_nb[(nb_nr + M + lr) * W + c + M] = v;
-            }
-            if (lr >= nr - M && dn_nb) dn_nb[(lr - (nr - M)) * W + c + M] = v;
+        for (int k = 1; k <= M; k++) {
+            lap = fmaf(ra.cf.ax[2][k], src[at - k] + src[at + k], lap);
+            lap = fmaf(ra.cf.ax[1][k], src[at - k * W] + src[at + k * W], lap);
         }
-        cluster.sync();
-    }
-
-    // the last state (step nt) and the one before it (step nt-1, or u^{t0}
-    // when nt == 1 -- the caller then skips out_prev)
-    for (int p = tid; p < npts; p += blockDim.x) {
-        const int lr = p / a.cols;
-        const int c = p - lr * a.cols;
-        const int at = (lr + M) * W + c + M;
-        const long long g = (long long)(r0 + lr) * a.s1 + c;
-        out_last[g] = ((nt & 1) ? buf1 : buf0)[at];
-        if (out_prev) out_prev[g] = ((nt & 1) ? buf0 : buf1)[at];
+        return fmaf(ra.adt, lap, u);
+    } else if (RULE == kRuleUpwind) {
+        const float u = src[at];
+        return u - ra.nux * (u - src[at - W]) - ra.nuy * (u - src[at - 1]);
+    } else {
+        const int cc = c == 0 ? 1 : (c == a.cols - 1 ? a.cols - 2 : c);
+        const int q = at + (cc - c);
+        if (gr == 0 || gr == a.rows - 1) return src[q];
+        return ra.wr * (src[q - W] + src[q + W]) + ra.wc * (src[q - 1] + src[q + 1]);
     }
 }
 
-template <int M>
-cudaError_t launch_cluster_m(const ClusterArgs &a, const Coef &cf, float adt, const float *u0, float *out_last,
-                             float *out_prev, int nt, size_t smem, cudaStream_t st)
+__device__ __forceinline__ double block_sum(double v, double *scratch)
 {
-    auto kern = diffusion_cluster_kernel<M>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += scratch[i];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+template <int RULE, int M>
+__global__ void __launch_bounds__(kCThreads, 1)
+    cluster_stencil_kernel(const ClusterArgs a, const RuleArgs ra, const float *__restrict__ u0, float *slot0,
+                           float *slot1, long long t0, long long nt, double tol, long long *res_steps,
+                           double *res_r)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char craw[];
+    const int W = a.width, H = a.halo;
+    const int HR = a.strip + 2 * H;  // rows held
+    float *buf[2];
+    buf[0] = reinterpret_cast<float *>(craw);
+    buf[1] = buf[0] + HR * W;
+    float *inbox = buf[1] + HR * W;                        // [2 parities][2 sides][H][cols]
+    double *part = reinterpret_cast<double *>(inbox + 4 * H * a.cols);  // [2] partial sums
+    double *scratch = part + 2;                            // [32]
+
+    const int r0 = (int)((long long)rank * a.rows / a.nctas);
+    const int r1 = (int)((long long)(rank + 1) * a.rows / a.nctas);
+    const int nr = r1 - r0;
+    const int tid = threadIdx.x;
+    const int tc = tid % a.tc, tr = tid / a.tc;
+    const bool lane_on = tr < a.tr;
+    const bool converge = RULE == kRuleJacobi && tol > 0.0;
+
+    // rows r0-H .. r1+H-1 of u^{t0} (zero outside the grid) into buf[0];
+    // buf[1] zero, so that rows outside the grid and the side columns stay 0
+    double s_mine = 0.0;
+    for (int q = tid; q < HR * W; q += blockDim.x) {
+        const int lr = q / W;
+        const int c = q - lr * W - a.hc;
+        const int gr = r0 - H + lr;
+        float v = 0.0f;
+        if (c >= 0 && c < a.cols && gr >= 0 && gr < a.rows && lr < nr + 2 * H) v = u0[(long long)gr * a.s1 + c];
+        buf[0][q] = v;
+        buf[1][q] = 0.0f;
+        if (converge && gr >= r0 && gr < r1 && c >= 0 && c < a.cols) s_mine += fabs((double)v);
+    }
+    double s_old = 0.0;
+    if (converge) {
+        const double t = block_sum(s_mine, scratch);
+        if (tid == 0) part[1] = t;
+    }
+    cluster.sync();
+    if (converge)
+        for (int k = 0; k < a.nctas; k++) s_old += *cluster.map_shared_rank(&part[1], k);
+
+    int cur = 0, par = 0;
+    long long done = 0;
+    double r_last = INFINITY;
+    bool stop = false;
+    while (done < nt && !stop) {
+        // the L1 criterion is taken after every sweep: blocks of one step
+        const int Kb = converge ? 1 : (int)((nt - done) < (long long)a.K ? (nt - done) : (long long)a.K);
+        s_mine = 0.0;
+        for (int j = 0; j < Kb; j++) {
+            const int ext = (Kb - 1 - j) * M;
+            const int lo = max(-ext, -r0), hi = min(nr + ext, a.rows - r0);
+            const float *src = buf[cur];
+            float *dst = buf[cur ^ 1];
+            if (lane_on) {
+                for (int lr = lo + tr; lr < hi; lr += a.tr) {
+                    const int base = (lr + H) * W + a.hc;
+                    const int gr = r0 + lr;
+                    for (int c = tc; c < a.cols; c += a.tc) {
+                        const float v = apply_rule<RULE, M>(src, base + c, W, gr, c, a, ra);
+                        dst[base + c] = v;
+                        if (converge && lr >= 0 && lr < nr) s_mine += fabs((double)v);
+                    }
+                }
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        done += Kb;
+        if (converge) {
+            const double t = block_sum(s_mine, scratch);
+            if (tid == 0) part[par] = t;
+        }
+        // first H rows to the neighbour above (its bottom inbox), last H rows
+        // to the neighbour below (its top inbox)
+        const int nH = H * a.cols;
+        if (a.nctas > 1 && (done < nt || converge)) {
+            float *up = rank > 0 ? cluster.map_shared_rank(inbox, rank - 1) + (par * 2 + 1) * nH : nullptr;
+            float *dn = rank + 1 < a.nctas ? cluster.map_shared_rank(inbox, rank + 1) + (par * 2 + 0) * nH : nullptr;
+            const float *s = buf[cur];
+            for (int q = tid; q < nH; q += blockDim.x) {
+                const int lr = q / a.cols, c = q - lr * a.cols;
+                if (up) up[q] = s[(lr + H) * W + a.hc + c];
+                if (dn) dn[q] = s[(nr - H + lr + H) * W + a.hc + c];
+            }
+        }
+        cluster.sync();
+        if (converge) {
+            double s_new = 0.0;
+            for (int k = 0; k < a.nctas; k++) s_new += *cluster.map_shared_rank(&part[par], k);
+            r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
+            s_old = s_new;
+            stop = r_last < tol;
+        }
+        if (a.nctas > 1 && done < nt && !stop) {
+            float *d = buf[cur];
+            const float *top = inbox + (par * 2 + 0) * nH, *bot = inbox + (par * 2 + 1) * nH;
+            for (int q = tid; q < nH; q += blockDim.x) {
+                const int lr = q / a.cols, c = q - lr * a.cols;
+                if (rank > 0) d[lr * W + a.hc + c] = top[q];
+                if (rank + 1 < a.nctas) d[(nr + H + lr) * W + a.hc + c] = bot[q];
+            }
+            __syncthreads();
+        }
+        par ^= 1;
+    }
+
+    // u^{t0+done} and u^{t0+done-1} into their slots
+    if (done > 0) {
+        float *last = ((t0 + done) & 1) ? slot1 : slot0;
+        float *prev = ((t0 + done - 1) & 1) ? slot1 : slot0;
+        for (int q = tid; q < nr * a.cols; q += blockDim.x) {
+            const int lr = q / a.cols, c = q - lr * a.cols;
+            const long long g = (long long)(r0 + lr) * a.s1 + c;
+            const int at = (lr + H) * W + a.hc + c;
+            last[g] = buf[cur][at];
+            prev[g] = buf[cur ^ 1][at];
+        }
+    }
+    if (rank == 0 && tid == 0 && res_steps) {
+        *res_steps = done;
+        *res_r = r_last;
+    }
+    // no CTA may leave while a neighbour can still read its shared memory
+    cluster.sync();
+}
+
+size_t cluster_smem_bytes(int strip, int halo, int width, int cols)
+{
+    return sizeof(float) * (2 * (size_t)(strip + 2 * halo) * width + 4 * (size_t)halo * cols) +
+           sizeof(double) * (2 + 32);
+}
+
+template <int RULE, int M>
+cudaError_t launch_rule(const ClusterPlan &p, const ClusterArgs &a, const RuleArgs &ra, const float *u0, float *s0,
+                        float *s1, long long t0, long long nt, double tol, long long *res_steps, double *res_r,
+                        cudaStream_t st)
+{
+    auto kern = cluster_stencil_kernel<RULE, M>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
-    if (a.nclusters > 8) {
+    if (a.nctas > 8) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)a.nclusters);
-    cfg.blockDim = dim3(kClusterThreads);
-    cfg.dynamicSmemBytes = smem;
+    cfg.gridDim = dim3((unsigned)a.nctas);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.dynamicSmemBytes = p.smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)a.nclusters;
+    attr[0].val.clusterDim.x = (unsigned)a.nctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a, cf, adt, u0, out_last, out_prev, nt);
+    return cudaLaunchKernelEx(&cfg, kern, a, ra, u0, s0, s1, t0, nt, tol, res_steps, res_r);
 }
 
-}  // namespace
-
-bool diffusion_cluster_fits(int M, const Geom &g, int *nclusters, size_t *smem_out)
+template <int RULE>
+cudaError_t launch_m(int M, const ClusterPlan &p, const ClusterArgs &a, const RuleArgs &ra, const float *u0,
+                     float *s0, float *s1, long long t0, long long nt, double tol, long long *rs, double *rr,
+                     cudaStream_t st)
 {
-    if (g.ndim != 2 || g.n[0] != 1 || M < 1 || M > kMaxHalfWidth) return false;
-    int dev = 0, smem_max = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    const int rows = (int)g.n[1], cols = (int)g.n[2];
-    const int width = (cols + 2 * M + 3) / 4 * 4;
-    for (int c : {8, 16}) {
-        const int strip = (rows + c - 1) / c;
-        if (rows / c < M) continue;  // every strip must cover its neighbours' halo
-        const size_t smem = sizeof(float) * 2 * (size_t)(strip + 2 * M) * width;
-        if (smem <= (size_t)smem_max) {
-            *nclusters = c;
-            *smem_out = smem;
-            return true;
+    if constexpr (RULE != kRuleDiffusion) {
+        if (M != 1) return cudaErrorInvalidValue;
+        return launch_rule<RULE, 1>(p, a, ra, u0, s0, s1, t0, nt, tol, rs, rr, st);
+    } else {
+        switch (M) {
+#define CASE(MM) \
+    case MM: return launch_rule<RULE, MM>(p, a, ra, u0, s0, s1, t0, nt, tol, rs, rr, st);
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
         }
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Whether a cluster of n CTAs with this shared memory can be resident (a
+// 16-CTA cluster needs 16 free SMs of one GPC).
+template <int RULE, int M>
+bool clusters_fit(int n, size_t smem)
+{
+    auto kern = cluster_stencil_kernel<RULE, M>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    if (n > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)n;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return num >= 1;
+}
+
+bool clusters_fit_rule(int rule, int M, int n, size_t smem)
+{
+    if (rule == kRuleUpwind) return M == 1 && clusters_fit<kRuleUpwind, 1>(n, smem);
+    if (rule == kRuleJacobi) return M == 1 && clusters_fit<kRuleJacobi, 1>(n, smem);
+    switch (M) {
+#define CASE(MM) \
+    case MM: return clusters_fit<kRuleDiffusion, MM>(n, smem);
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
     }
     return false;
 }
 
-cudaError_t launch_diffusion_cluster(int M, const Geom &g, const Coef &cf, float adt, const float *u0,
-                                     float *out_last, float *out_prev, int nt, int nclusters, size_t smem,
-                                     cudaStream_t st)
+ClusterArgs make_args(const ClusterPlan &p, const Geom &g)
 {
     ClusterArgs a;
     a.rows = (int)g.n[1];
     a.cols = (int)g.n[2];
     a.s1 = g.s1;
-    a.nclusters = nclusters;
-    a.strip = (a.rows + nclusters - 1) / nclusters;
-    a.width = (a.cols + 2 * M + 3) / 4 * 4;
-    switch (M) {
-#define CASE(MM) \
-    case MM: return launch_cluster_m<MM>(a, cf, adt, u0, out_last, out_prev, nt, smem, st);
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
-#undef CASE
+    a.nctas = p.nctas;
+    a.strip = (a.rows + p.nctas - 1) / p.nctas;
+    a.hc = p.M;
+    a.width = (a.cols + 2 * a.hc + 3) / 4 * 4;
+    a.K = p.K;
+    a.halo = p.halo;
+    a.tc = std::min(kCThreads, (a.cols + 31) / 32 * 32);
+    a.tr = kCThreads / a.tc;
+    return a;
+}
+
+}  // namespace
+
+// Pick the cluster size and the steps per exchange of a rule on a 2D grid:
+// the fewest CTAs that keep at most ~8 points per thread and step (tiny grids
+// stay in one CTA, where a block barrier is cheaper than a cluster one), else
+// the most that fit; K = `want_k` if > 0, else 1 + strip/(4M) (at most ~25 %
+// redundant rows), capped at 8 and so that every strip covers the halo.
+bool cluster_plan_build(int rule, int M, const Geom &g, int want_k, ClusterPlan *out)
+{
+    out->ok = false;
+    if (g.ndim != 2 || g.n[0] != 1 || M < 1 || M > kMaxHalfWidth) return false;
+    if (rule != kRuleDiffusion && M != 1) return false;
+    int dev = 0, smem_max = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    const int rows = (int)g.n[1], cols = (int)g.n[2];
+    if (rows < 1 || cols < 1 || (rule == kRuleJacobi && (rows < 3 || cols < 3))) return false;
+    const int width = (cols + 2 * M + 3) / 4 * 4;
+    const long long pts = (long long)rows * cols;
+    int chosen = 0;
+    for (int n : {1, 2, 4, 8, 16}) {
+        const int strip = (rows + n - 1) / n;
+        const int min_strip = rows / n;
+        int K = want_k > 0 ? want_k : std::min(8, 1 + min_strip / (4 * M));
+        if (n == 1) K = want_k > 0 ? want_k : 64;
+        const int halo = n == 1 ? M : K * M;
+        if (n > 1 && min_strip < halo) continue;
+        const size_t smem = cluster_smem_bytes(strip, halo, width, cols);
+        if (smem > (size_t)smem_max || !clusters_fit_rule(rule, M, n, smem)) continue;
+        ClusterPlan p;
+        p.ok = true;
+        p.rule = rule;
+        p.M = M;
+        p.nctas = n;
+        p.K = K;
+        p.halo = halo;
+        p.smem = smem;
+        *out = p;
+        chosen = n;
+        if ((pts + n - 1) / n <= 8LL * kCThreads) break;
+    }
+    return chosen > 0;
+}
+
+cudaError_t launch_cluster_run(const ClusterPlan &p, const Geom &g, const Coef &cf, float adt, float nux, float nuy,
+                               float wr, float wc, const float *u0, float *slot0, float *slot1, long long t0,
+                               long long nt, double tol, long long *res_steps, double *res_r, cudaStream_t st)
+{
+    const ClusterArgs a = make_args(p, g);
+    RuleArgs ra;
+    ra.cf = cf;
+    ra.adt = adt;
+    ra.nux = nux;
+    ra.nuy = nuy;
+    ra.wr = wr;
+    ra.wc = wc;
+    switch (p.rule) {
+    case kRuleDiffusion:
+        return launch_m<kRuleDiffusion>(p.M, p, a, ra, u0, slot0, slot1, t0, nt, tol, res_steps, res_r, st);
+    case kRuleUpwind:
+        return launch_m<kRuleUpwind>(p.M, p, a, ra, u0, slot0, slot1, t0, nt, tol, res_steps, res_r, st);
+    case kRuleJacobi:
+        return launch_m<kRuleJacobi>(p.M, p, a, ra, u0, slot0, slot1, t0, nt, tol, res_steps, res_r, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -176,6 +176,68 @@ __global__ void diffusion_plain_kernel(Geom g, Coef cf, float adt, const float *
     }
 }
 
+// Linear Convection (Eq. 2dconvdiscr) on a 2D grid (rows d1 = x, columns
+// d2 = y): first-order upwind, zero halo.  One thread per point.
+__global__ void convection_plain_kernel(Geom g, float nux, float nuy, const float *__restrict__ u,
+                                        float *__restrict__ out)
+{
+    const int64_t i2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i1 = blockIdx.y;
+    if (i2 >= g.n[2]) return;
+    const int64_t at = i1 * g.s1 + i2;
+    const float uc = u[at];
+    const float ux = i1 > 0 ? u[at - g.s1] : 0.0f;
+    const float uy = i2 > 0 ? u[at - 1] : 0.0f;
+    out[at] = uc - nux * (uc - ux) - nuy * (uc - uy);
+}
+
+__device__ __forceinline__ void add_block_sum(double v, double *sum)
+{
+    __shared__ double part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)((blockDim.x + 31) >> 5); i++) t += part[i];
+        atomicAdd(sum, t);
+    }
+}
+
+// Laplace equation (Eq. 2dlaplace_discr) Jacobi sweep with the boundary
+// expressions: rows 0 and n1-1 keep their values (Dirichlet), then columns 0
+// and n2-1 copy columns 1 and n2-2 (Neumann, corners included).
+__global__ void jacobi_plain_kernel(Geom g, float wr, float wc, const float *__restrict__ p,
+                                    float *__restrict__ out, double *sum)
+{
+    const int64_t i2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i1 = blockIdx.y;
+    float v = 0.0f;
+    if (i2 < g.n[2]) {
+        const int64_t cc = i2 == 0 ? 1 : (i2 == g.n[2] - 1 ? g.n[2] - 2 : i2);
+        const int64_t q = i1 * g.s1 + cc;
+        if (i1 == 0 || i1 == g.n[1] - 1)
+            v = p[q];
+        else
+            v = wr * (p[q - g.s1] + p[q + g.s1]) + wc * (p[q - 1] + p[q + 1]);
+        out[i1 * g.s1 + i2] = v;
+    }
+    if (sum) add_block_sum(fabs((double)v), sum);
+}
+
+__global__ void abs_sum_kernel(Geom g, const float *__restrict__ u, double *sum)
+{
+    double t = 0.0;
+    const int64_t total = g.n[0] * g.n[1] * g.n[2];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i2 = q % g.n[2], r = q / g.n[2];
+        const int64_t i1 = r % g.n[1], i0 = r / g.n[1];
+        t += fabs((double)u[i0 * g.s0 + i1 * g.s1 + i2]);
+    }
+    add_block_sum(t, sum);
+}
+
 int grid_stride_blocks(int64_t total)
 {
     int64_t b = (total + kThreads - 1) / kThreads;
@@ -268,6 +330,28 @@ cudaError_t launch_diffusion_plain(int M, const Geom &g, const Coef &cf, float a
     default:
         return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convection_plain(const Geom &g, float nux, float nuy, const float *u, float *out,
+                                    cudaStream_t st)
+{
+    dim3 grid((unsigned)((g.n[2] + 127) / 128), (unsigned)g.n[1]);
+    convection_plain_kernel<<<grid, 128, 0, st>>>(g, nux, nuy, u, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_plain(const Geom &g, float wr, float wc, const float *p, float *out, double *sum,
+                                cudaStream_t st)
+{
+    dim3 grid((unsigned)((g.n[2] + 127) / 128), (unsigned)g.n[1]);
+    jacobi_plain_kernel<<<grid, 128, 0, st>>>(g, wr, wc, p, out, sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_abs_sum(const Geom &g, const float *u, double *sum, cudaStream_t st)
+{
+    abs_sum_kernel<<<grid_stride_blocks(g.n[0] * g.n[1] * g.n[2]), kThreads, 0, st>>>(g, u, sum);
     return cudaGetLastError();
 }
 

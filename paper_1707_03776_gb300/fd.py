@@ -26,6 +26,8 @@ FD_ERR_NOMEM = 8
 
 FD_DIFFUSION_EULER = 1
 FD_ACOUSTIC_LEAPFROG = 2
+FD_CONVECTION_UPWIND = 3
+FD_LAPLACE_JACOBI = 4
 
 FD_FLAG_REVERSE = 1 << 0
 FD_FLAG_NO_CFL_CHECK = 1 << 1
@@ -100,6 +102,10 @@ _SIGNATURES = [
     ("fd_cnn_mse_grad", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     ("fd_cnn_adam", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64, _vp]),
+    ("fd_operator_converge", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+    ("fd_operator_set_time_block", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("fd_operator_get_time_block", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -333,6 +339,25 @@ def fd_batch_destroy(b):
     lib().fd_batch_destroy(b)
 
 
+def fd_operator_converge(op, t0, max_iter, tol):
+    """Laplace convergence loop; returns (sweeps done, last r)."""
+    it = ctypes.c_int64(0)
+    r = ctypes.c_double(0.0)
+    _check(lib().fd_operator_converge(op, int(t0), int(max_iter), float(tol), ctypes.byref(it), ctypes.byref(r)))
+    return int(it.value), float(r.value)
+
+
+def fd_operator_set_time_block(op, k):
+    _check(lib().fd_operator_set_time_block(op, int(k)))
+
+
+def fd_operator_get_time_block(op):
+    k = ctypes.c_int(0)
+    n = ctypes.c_int(0)
+    _check(lib().fd_operator_get_time_block(op, ctypes.byref(k), ctypes.byref(n)))
+    return k.value, n.value
+
+
 def _ptr(t):
     return None if t is None else (t if isinstance(t, int) else t.data_ptr())
 
@@ -532,6 +557,10 @@ class Operator:
 
     def sync(self):
         fd_operator_sync(self.handle)
+
+    def converge(self, t0, max_iter, tol):
+        """The Laplace example's convergence loop: (sweeps done, last r)."""
+        return fd_operator_converge(self.handle, t0, max_iter, tol)
 
     @property
     def launches(self):

@@ -365,3 +365,35 @@ def closure_training_set(count=128, n_coarse=64, nt=600, f0=8.0, first=160, ever
     does not see the source, learns the propagation error)."""
     cfgs = [closure_config(n_coarse, nt, seed=s, f0=f0) for s in range(count)]
     return cfgs, list(range(first, nt - 2, every))
+
+
+def smooth_bump(s):
+    """C-infinity bump on (0, 1): exp(1 - 1/(1 - (2s-1)^2)), peak 1 at s = 1/2."""
+    s = np.asarray(s, dtype=np.float64)
+    t = 2.0 * s - 1.0
+    out = np.zeros_like(s)
+    inside = np.abs(t) < 1.0
+    out[inside] = np.exp(1.0 - 1.0 / (1.0 - t[inside] ** 2))
+    return out
+
+
+def convection_config(n=81, c=1.0, courant=0.2, nt=100, extent=2.0):
+    """The Linear Convection example: an n x n grid on [0, extent]^2 (x = the
+    first axis), velocity c, dt = courant * dx / c, nt steps.  The paper's
+    smooth initial condition 1 + b(2x/3) b(2y/3) (its 1D profile is garbled
+    in the text; b is the C-infinity bump above) is stored as its deviation
+    from the far-field value 1, so that the zero halo is the inflow value."""
+    h = extent / (n - 1)
+    x = np.arange(n) * h
+    w0 = smooth_bump(2.0 * x / 3.0)[:, None] * smooth_bump(2.0 * x / 3.0)[None, :]
+    return dict(shape=(n, n), spacing=(h, h), c=c, dt=courant * h / c, nt=nt, u0=w0.astype(np.float32))
+
+
+def laplace_config(nx=31, ny=31, lx=2.0, ly=1.0, tol=1e-4):
+    """The Laplace example: nx x ny nodes on [0, lx] x [0, ly], p = 0
+    initially, p = 0 on x = 0 and p = y on x = lx (bc_right), dp/dy = 0 on
+    y = 0 and y = ly, stopped when the L1 criterion falls below tol."""
+    dx, dy = lx / (nx - 1), ly / (ny - 1)
+    p0 = np.zeros((nx, ny), dtype=np.float64)
+    p0[-1, :] = np.arange(ny) * dy
+    return dict(shape=(nx, ny), spacing=(dx, dy), p0=p0.astype(np.float32), tol=tol)

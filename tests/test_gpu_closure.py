@@ -342,14 +342,15 @@ def test_closure_rollout_parity():
 
 
 def test_training_lowers_loss_and_trace_error():
-    """Training on 32 layered-model runs lowers the one-step loss, and the
+    """Training on 32 layered-model runs lowers the one-step loss tenfold, and the
     trained closure's receiver traces are closer to the fine grid's than the
     plain coarse run's on an unseen model (smaller than the evaluation
     workload; the full-size numbers come from bench.py)."""
     _torch()
     from paper_1707_03776_gb300 import closure, workloads as wl
-    net, data, hist = closure.train_default(count=32, n_coarse=48, nt=500, iters=600, log_every=100)
-    assert hist[-1][1] < 0.1 * hist[0][1]
+    net, data, hist = closure.train_default(count=32, n_coarse=64, nt=600, iters=800, log_every=100)
+    # first entry: the untrained network's loss; last: the mean of the last 100
+    assert hist[-1][1] < 0.1 * hist[0][1], hist
     cfg = wl.closure_config(64, 800, seed=1000, src="surface")
     ref = closure.FineReference(cfg).run().cpu().numpy()
     op = closure.ClosureOperator(cfg, net)
