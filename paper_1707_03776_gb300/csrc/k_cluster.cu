@@ -127,6 +127,17 @@ __global__ void __launch_bounds__(kCThreads, 1)
     const int tc = tid % a.tc, tr = tid / a.tc;
     const bool lane_on = tr < a.tr;
     const bool converge = RULE == kRuleJacobi && tol > 0.0;
+    // a cluster of one CTA needs only block barriers and its own shared memory
+    const bool alone = a.nctas == 1;
+    auto barrier = [&]() {
+        if (alone)
+            __syncthreads();
+        else
+            cluster.sync();
+    };
+    auto part_of = [&](int k, int slot) -> double {
+        return alone ? part[slot] : *cluster.map_shared_rank(&part[slot], k);
+    };
 
     // rows r0-H .. r1+H-1 of u^{t0} (zero outside the grid) into buf[0];
     // buf[1] zero, so that rows outside the grid and the side columns stay 0
@@ -146,9 +157,9 @@ __global__ void __launch_bounds__(kCThreads, 1)
         const double t = block_sum(s_mine, scratch);
         if (tid == 0) part[1] = t;
     }
-    cluster.sync();
+    barrier();
     if (converge)
-        for (int k = 0; k < a.nctas; k++) s_old += *cluster.map_shared_rank(&part[1], k);
+        for (int k = 0; k < a.nctas; k++) s_old += part_of(k, 1);
 
     int cur = 0, par = 0;
     long long done = 0;
@@ -195,10 +206,10 @@ __global__ void __launch_bounds__(kCThreads, 1)
                 if (dn) dn[q] = s[(nr - H + lr + H) * W + a.hc + c];
             }
         }
-        cluster.sync();
+        barrier();
         if (converge) {
             double s_new = 0.0;
-            for (int k = 0; k < a.nctas; k++) s_new += *cluster.map_shared_rank(&part[par], k);
+            for (int k = 0; k < a.nctas; k++) s_new += part_of(k, par);
             r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
             s_old = s_new;
             stop = r_last < tol;
@@ -233,7 +244,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
         *res_r = r_last;
     }
     // no CTA may leave while a neighbour can still read its shared memory
-    cluster.sync();
+    barrier();
 }
 
 size_t cluster_smem_bytes(int strip, int halo, int width, int cols)
