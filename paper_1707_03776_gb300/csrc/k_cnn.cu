@@ -61,6 +61,12 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Shared-memory position (in 16-byte chunks) of channel half h of plane
+// point pt: the halves of points whose index has bit 2 set are exchanged, so
+// that the 8 row addresses of an ldmatrix phase (8 consecutive points, any
+// start) fall in 8 distinct 16-byte bank groups.
+__device__ __forceinline__ int chunk_of(int pt, int h) { return 2 * pt + (h ^ ((pt >> 2) & 1)); }
+
 // Load input plane z (all 16 channels, rows row0-1.., points col0-1..) into
 // ring slot `slot`; out-of-grid points are zero.
 __device__ __forceinline__ void load_plane(uint32_t *ring, int slot, const __nv_bfloat16 *x, const CnnDims &d,
@@ -74,14 +80,21 @@ __device__ __forceinline__ void load_plane(uint32_t *ring, int slot, const __nv_
         const int gy = row0 - 1 + rr, gx = col0 - 1 + cc;
         const bool ok = zin && gy >= 0 && gy < d.n1 && gx >= 0 && gx < d.n2;
         const __nv_bfloat16 *src = ok ? x + (((long long)z * d.n1 + gy) * d.n2 + gx) * kC + half * 8 : x;
-        cp_async16(smem_u32(dst + pt * (kC / 2) + half * 4), src, ok);
+        cp_async16(smem_u32(dst + chunk_of(pt, half) * 4), src, ok);
     }
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
 }
 
 // y = act(conv(x, w) + b) [* (mask > 0)].  NT output-channel groups of 8.
 // OUT_F32: write channel 0 as FP32 (the network's output), else BF16 x 16.
 template <int NT, bool RELU, bool MASK, bool OUT_F32>
-__global__ void __launch_bounds__(32 * kT1)
+__global__ void __launch_bounds__(32 * kT1, 2)
     conv3d_kernel(const __nv_bfloat16 *__restrict__ x, const uint2 *__restrict__ wfrag,
                   const float *__restrict__ bias, int cout, const __nv_bfloat16 *__restrict__ mask, void *y,
                   CnnDims d)
@@ -96,6 +109,11 @@ __global__ void __launch_bounds__(32 * kT1)
     const int z1 = min(d.n0, z0 + kZc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tig = lane & 3;
+    // ldmatrix row of this lane: matrix lane/8 (0: points 0-7 channels 0-7,
+    // 1: points 8-15 channels 0-7, 2: points 0-7 channels 8-15, 3: points
+    // 8-15 channels 8-15), row lane%8
+    const int lm_pt = ((lane >> 3) & 1) * 8 + (lane & 7);
+    const int lm_half = lane >> 4;
 
     for (int q = threadIdx.x; q < 27 * NT * 32; q += blockDim.x) sw[q] = wfrag[q];
     load_plane(ring, (z0 - 1 + kRing) % kRing, x, d, z0 - 1, row0, col0);
@@ -111,6 +129,7 @@ __global__ void __launch_bounds__(32 * kT1)
         bv[nt][0] = (bias && o < cout) ? bias[o] : 0.f;
         bv[nt][1] = (bias && o + 1 < cout) ? bias[o + 1] : 0.f;
     }
+    const uint32_t ring_base = smem_u32(ring);
 
     for (int z = z0; z < z1; z++) {
         // plane z+2 in flight while z is computed; z+1 must have landed
@@ -128,21 +147,27 @@ __global__ void __launch_bounds__(32 * kT1)
                 for (int e = 0; e < 4; e++) acc[mt][nt][e] = 0.f;
 
 #pragma unroll 1
-        for (int t = 0; t < 27; t++) {
-            const int a = t / 9 - 1, b = (t / 3) % 3 - 1, c = t % 3 - 1;
-            const uint32_t *pl = ring + ((z + a + kRing) % kRing) * kPlanePts * (kC / 2);
-            // local point (row warp+1+b, col p+1+c)
-            const uint32_t *rowp = pl + ((warp + 1 + b) * (kT2 + 2) + 1 + c) * (kC / 2);
-            uint2 bw[NT];
+        for (int a = -1; a <= 1; a++) {
+            const uint32_t plane = ring_base + (uint32_t)(((z + a + kRing) % kRing) * kPlanePts * (kC / 2) * 4);
 #pragma unroll
-            for (int nt = 0; nt < NT; nt++) bw[nt] = sw[(t * NT + nt) * 32 + lane];
+            for (int b = -1; b <= 1; b++) {
 #pragma unroll
-            for (int mt = 0; mt < 4; mt++) {
-                const uint32_t *p0 = rowp + (mt * 16 + g) * (kC / 2) + tig;
-                const uint32_t *p1 = p0 + 8 * (kC / 2);
-                const uint32_t a0 = p0[0], a1 = p1[0], a2 = p0[4], a3 = p1[4];
+                for (int c = -1; c <= 1; c++) {
+                    const int t = (a + 1) * 9 + (b + 1) * 3 + (c + 1);
+                    uint2 bw[NT];
 #pragma unroll
-                for (int nt = 0; nt < NT; nt++) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt].x, bw[nt].y);
+                    for (int nt = 0; nt < NT; nt++) bw[nt] = sw[(t * NT + nt) * 32 + lane];
+                    // first point of this warp's row for the tap
+                    const int pt0 = (warp + 1 + b) * (kT2 + 2) + 1 + c;
+#pragma unroll
+                    for (int mt = 0; mt < 4; mt++) {
+                        const int pt = pt0 + mt * 16 + lm_pt;
+                        uint32_t a0, a1, a2, a3;
+                        ldmatrix_x4(plane + (uint32_t)(chunk_of(pt, lm_half) * 16), a0, a1, a2, a3);
+#pragma unroll
+                        for (int nt = 0; nt < NT; nt++) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bw[nt].x, bw[nt].y);
+                    }
+                }
             }
         }
 
