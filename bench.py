@@ -244,10 +244,25 @@ def bench_diffusion(steps=5, warmup=3):
     ms = e0.elapsed_time(e1) / steps
     pts = float(cfg["shape"][0] * cfg["shape"][1]) * cfg["nt"]
     k, ctas = fd.fd_operator_get_time_block(op.handle)
+    import oracle
+    cpu = _cpu_oracle(lambda: oracle.diffusion(cfg["u0"], cfg["spacing"], 2, cfg["a"], cfg["dt"], cfg["nt"],
+                                               precision="f32"), pts, "GPts/s", "the whole 500-step run, FP32")
     return {"workload": "diffusion2d_256^2_ring_so2_nt500", "value": pts / (ms * 1e-3) / 1e9, "unit": "GPts/s",
             "ms_per_run": ms, "us_per_time_step": 1e3 * ms / cfg["nt"],
             "launches_per_run": (op.launches - n0) / steps, "cluster_ctas": ctas, "steps_per_exchange": k,
-            "bound": "latency (grid held in one cluster's shared memory)"}
+            "bound": "latency (grid held in one cluster's shared memory)", "cpu_oracle": cpu}
+
+
+def _cpu_oracle(fn, pts, unit, sample):
+    """Time one bounded oracle call on the host cores (a reported baseline
+    beside each row, not a target)."""
+    import oracle
+    oracle._lib()
+    t = time.perf_counter()
+    fn()
+    el = time.perf_counter() - t
+    return {"value": pts / el / 1e9, "unit": unit, "cores": oracle.num_threads(), "kind": "oracle",
+            "s": el, "sample": sample}
 
 
 def _time_runs(fn, reps, warmup=3):
@@ -289,7 +304,10 @@ def bench_convection(reps=20):
             k, ctas = fd.fd_operator_get_time_block(op.handle)
         op.sync()
     pts = float(cfg["shape"][0] * cfg["shape"][1]) * cfg["nt"]
-    return {"workload": "convection2d_81^2_c1_nt100", "value": pts / (out["cluster"] * 1e-3) / 1e9,
+    import oracle
+    cpu = _cpu_oracle(lambda: oracle.convection(cfg["u0"], cfg["spacing"], cfg["c"], cfg["dt"], cfg["nt"],
+                                                precision="f32"), pts, "GPts/s", "the whole 100-step run, FP32")
+    return {"cpu_oracle": cpu, "workload": "convection2d_81^2_c1_nt100", "value": pts / (out["cluster"] * 1e-3) / 1e9,
             "unit": "GPts/s", "ms_per_run": out["cluster"], "us_per_time_step": 1e3 * out["cluster"] / cfg["nt"],
             "plain_ms_per_run": out["plain"], "speedup_vs_plain": out["plain"] / out["cluster"],
             "cluster_ctas": ctas, "steps_per_exchange": k}
@@ -323,7 +341,12 @@ def bench_laplace(reps=5):
             run()
         out[name] = ((time.perf_counter() - t0) / reps * 1e3, res[-1])
     it = out["cluster"][1][0]
-    return {"workload": "laplace2d_31^2_tol1e-4", "unit": "ms to convergence", "value": out["cluster"][0],
+    import oracle
+    npts = float(cfg["shape"][0] * cfg["shape"][1]) * it
+    cpu = _cpu_oracle(lambda: oracle.laplace(cfg["p0"], cfg["spacing"], cfg["tol"], 1000000, precision="f32"),
+                      npts, "GPts/s (sweeps x points / s)", "the whole convergence loop, FP32")
+    cpu["ms"] = cpu["s"] * 1e3
+    return {"cpu_oracle": cpu, "workload": "laplace2d_31^2_tol1e-4", "unit": "ms to convergence", "value": out["cluster"][0],
             "sweeps": it, "r_last": out["cluster"][1][1], "us_per_sweep": 1e3 * out["cluster"][0] / it,
             "plain_ms": out["plain"][0], "plain_sweeps": out["plain"][1][0],
             "speedup_vs_plain": out["plain"][0] / out["cluster"][0]}
@@ -369,12 +392,20 @@ def bench_gradient(n=256, nt=1500, k=50, shots=1):
     g_t, g_p = grads["tiled"], grads["plain"]
     rel = float((g_t - g_p).norm() / g_p.norm())
     pts = float(n) ** 3 * nt
+    import oracle
+    sc = wl.gradient_config(n=64, nt=100, nrec_side=17, sponge=10)
+    nrec = sc["rec_coords"].shape[0]
+    cpu = _cpu_oracle(lambda: oracle.acoustic_gradient(
+        sc["shape"], sc["spacing"], sc["origin"], 8, sc["m0"].astype(np.float64), sc["eta"].astype(np.float64),
+        sc["dt"], 100, sc["shots"][0], sc["wavelet"][:100], sc["rec_coords"], np.zeros((100, nrec))),
+        64.0 ** 3 * 100, "GPts/s (grid points x steps / s of forward+adjoint+imaging)",
+        "64^3 SO8, 100 steps, 17x17 receivers, FP64 loop nest keeping the whole history")
     return {"workload": "gradient3d_%d^3_so8_nt%d_65x65rec_ckpt%d" % (n, nt, k),
             "value": pts / out["tiled"]["s_per_shot_gradient"] / 1e9, "unit": "GPts/s (grid points x steps "
             "of the modelled shot per second of forward+adjoint+imaging)",
             "s_per_shot": out["tiled"]["s_per_shot_gradient"], "plain_s_per_shot": out["plain"]["s_per_shot_gradient"],
             "speedup_vs_plain": out["plain"]["s_per_shot_gradient"] / out["tiled"]["s_per_shot_gradient"],
-            "grad_rel_diff_vs_plain": rel, "loss": out["tiled"]["loss"]}
+            "grad_rel_diff_vs_plain": rel, "loss": out["tiled"]["loss"], "cpu_oracle": cpu}
 
 
 def bench_batched(nshots=64, nt=800, plain_shots=8):
@@ -454,7 +485,13 @@ def bench_batched(nshots=64, nt=800, plain_shots=8):
     traces_b = [s["rec"].data[:, :s["rec"].npoint] for s in shots[:plain_shots]]
     err = max(float((a - b).norm() / b.norm()) for a, b in zip(traces_b, traces_plain))
     err_seq = max(float((a - b).norm() / b.norm()) for a, b in zip(traces_b, traces_seq))
-    return {"workload": "batched_%dshots_windows160-320_of_512^3_so8_nt%d" % (nshots, nt),
+    import oracle
+    shape0, m0_, eta0, src0, rec0 = wl.window_shot(cfg, 0)
+    cpu = _cpu_oracle(lambda: oracle.acoustic_forward(shape0, cfg["spacing"], (0.0, 0.0, 0.0), 8, m0_, eta0, dt, 3,
+                                                      src_coords=src0, src_trace=cfg["wavelet"], rec_coords=rec0,
+                                                      n_total=nt, precision="f32"),
+                      float(np.prod(shape0)) * 3, "GPts/s", "3 steps of the first window %s, FP32" % (shape0,))
+    return {"cpu_oracle": cpu, "workload": "batched_%dshots_windows160-320_of_512^3_so8_nt%d" % (nshots, nt),
             "value": pts / t_graph / 1e9, "unit": "GPts/s (sum of window points x steps / s)",
             "s_batch_graph": t_graph, "s_batch_eager": t_batch, "s_sequential_tiled": t_seq,
             "s_sequential_plain_est": t_plain_sub * pts / pts_sub,
@@ -524,6 +561,12 @@ def bench_learned(n=128, nt=2000):
     flops_mma = 2.0 * 27 * pts * 16 * (16 * 3 + 8)  # K padded to 16 channels, the last layer's N to 8
     peak, kind = measured_peak_bf16()
     achieved = flops / (ms_net * 1e-3) / 1e12
+    from oracle import cnn
+    wts = [(w.astype(np.float64), np.zeros(w.shape[2])) for w in net.weights()]
+    xs = np.random.default_rng(0).standard_normal((32, 32, 32, 6))
+    cpu = _cpu_oracle(lambda: cnn.network_forward(xs, wts), 2.0 * 27 * 32 ** 3 * sum(
+        ch[i] * ch[i + 1] for i in range(len(ch) - 1)) / 1e3, "TFLOP/s",
+        "network forward on 32^3 points, numpy FP64")
     return {"workload": "closure_coarse%d^3_20m_so4_fine%d^3_10m_so16_nt%d_layered" % (n, 2 * n - 1, nt),
             "unit": "s per modelled shot; trace errors relative to the fine grid",
             "trace_rel_err_learned": err, "trace_rel_err_plain_coarse": plain,
@@ -532,6 +575,7 @@ def bench_learned(n=128, nt=2000):
             "train": {"s": t_train, "samples": data.n, "models": 128, "iters": 800, "rho": net.rho,
                       "loss_first_last": [hist[0][1], hist[-1][1]]},
             "network_ms_per_step": ms_net, "network_share_of_learned_step": ms_net * nt / 1e3 / t_learned,
+            "cpu_oracle": cpu,
             "roofline": {"bound": "tensor", "kernel": "conv3d (implicit GEMM, mma.sync m16n8k16 BF16/FP32)",
                          "achieved": achieved, "achieved_mma_issued": flops_mma / (ms_net * 1e-3) / 1e12,
                          "peak": peak, "peak_kind": kind, "unit": "TFLOP/s", "frac": achieved / peak}}

@@ -210,9 +210,12 @@ __global__ void __launch_bounds__(kCThreads, 1)
         if (converge) {
             double s_new = 0.0;
             for (int k = 0; k < a.nctas; k++) s_new += part_of(k, par);
-            r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
+            // r < tol without a division (FP64 division is slow here); r
+            // itself is formed once, by the thread that reports it
+            stop = s_old > 0.0 && fabs(s_new - s_old) < tol * s_old;
+            if ((stop || done >= nt) && rank == 0 && tid == 0)
+                r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
             s_old = s_new;
-            stop = r_last < tol;
         }
         if (a.nctas > 1 && done < nt && !stop) {
             float *d = buf[cur];
