@@ -24,9 +24,10 @@
 //              first and last columns copy their neighbour column (Neumann,
 //              corners included) -- in the order the paper lists them.
 // The jacobi rule can stop on the L1 criterion r = |S+ - S| / S < tol, with S
-// the grid's sum of |p| in FP64: every CTA adds its rows' partial sum to a
-// slot of its shared memory, and after the barrier every CTA reads all slots
-// in rank order, so all take the same decision.
+// the grid's sum of |p|: every CTA adds its rows' partial sum (compensated
+// FP32, ~48 significant bits) to a slot of its shared memory, and after the
+// barrier thread 0 of every CTA adds all slots in rank order in FP64, so all
+// take the same decision.
 //
 // Grid data touches global memory only at the start (u^{t0}) and at the end:
 // the last state goes to slot (t0+steps)%2 and the one before it to the other
@@ -89,17 +90,40 @@ __device__ __forceinline__ float apply_rule(const float *__restrict__ src, int a
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double *scratch)
+// Compensated FP32 sum (hi + lo carries ~48 significant bits): Knuth's
+// TwoSum of the high parts, the rounding error folded into the low part.
+// FP64 arithmetic is slow on this GPU; the convergence sums only need ~1e-12.
+__device__ __forceinline__ void sum2_add(float &hi, float &lo, float bhi, float blo)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const float s = hi + bhi;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (bhi - bp);
+    lo = lo + blo + e;
+    hi = s;
+}
+
+// Block-wide compensated sum; the result (as FP64) is valid in thread 0.
+__device__ __forceinline__ double block_sum2(float hi, float lo, float *scratch)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        sum2_add(hi, lo, oh, ol);
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) scratch[w] = v;
+    if (l == 0) {
+        scratch[2 * w] = hi;
+        scratch[2 * w + 1] = lo;
+    }
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += scratch[i];
+    if (threadIdx.x == 0) {
+        float h = 0.0f, q = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) sum2_add(h, q, scratch[2 * i], scratch[2 * i + 1]);
+        t = (double)h + (double)q;
+    }
     __syncthreads();
-    return t;  // valid in thread 0
+    return t;
 }
 
 template <int RULE, int M>
@@ -118,7 +142,8 @@ __global__ void __launch_bounds__(kCThreads, 1)
     buf[1] = buf[0] + HR * W;
     float *inbox = buf[1] + HR * W;                        // [2 parities][2 sides][H][cols]
     double *part = reinterpret_cast<double *>(inbox + 4 * H * a.cols);  // [2] partial sums
-    double *scratch = part + 2;                            // [32]
+    float *scratch = reinterpret_cast<float *>(part + 2);  // [32 warps][hi, lo]
+    volatile int *flag = reinterpret_cast<volatile int *>(scratch + 64);
 
     const int r0 = (int)((long long)rank * a.rows / a.nctas);
     const int r1 = (int)((long long)(rank + 1) * a.rows / a.nctas);
@@ -141,7 +166,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
 
     // rows r0-H .. r1+H-1 of u^{t0} (zero outside the grid) into buf[0];
     // buf[1] zero, so that rows outside the grid and the side columns stay 0
-    double s_mine = 0.0;
+    float sh = 0.0f, sl = 0.0f;
     for (int q = tid; q < HR * W; q += blockDim.x) {
         const int lr = q / W;
         const int c = q - lr * W - a.hc;
@@ -150,15 +175,17 @@ __global__ void __launch_bounds__(kCThreads, 1)
         if (c >= 0 && c < a.cols && gr >= 0 && gr < a.rows && lr < nr + 2 * H) v = u0[(long long)gr * a.s1 + c];
         buf[0][q] = v;
         buf[1][q] = 0.0f;
-        if (converge && gr >= r0 && gr < r1 && c >= 0 && c < a.cols) s_mine += fabs((double)v);
+        if (converge && gr >= r0 && gr < r1 && c >= 0 && c < a.cols) sum2_add(sh, sl, fabsf(v), 0.0f);
     }
+    // the convergence state lives in thread 0 of every CTA (all take the same
+    // decision from the same partial sums) and reaches the others by `flag`
     double s_old = 0.0;
     if (converge) {
-        const double t = block_sum(s_mine, scratch);
+        const double t = block_sum2(sh, sl, scratch);
         if (tid == 0) part[1] = t;
     }
     barrier();
-    if (converge)
+    if (converge && tid == 0)
         for (int k = 0; k < a.nctas; k++) s_old += part_of(k, 1);
 
     int cur = 0, par = 0;
@@ -168,7 +195,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
     while (done < nt && !stop) {
         // the L1 criterion is taken after every sweep: blocks of one step
         const int Kb = converge ? 1 : (int)((nt - done) < (long long)a.K ? (nt - done) : (long long)a.K);
-        s_mine = 0.0;
+        sh = sl = 0.0f;
         for (int j = 0; j < Kb; j++) {
             const int ext = (Kb - 1 - j) * M;
             const int lo = max(-ext, -r0), hi = min(nr + ext, a.rows - r0);
@@ -181,7 +208,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
                     for (int c = tc; c < a.cols; c += a.tc) {
                         const float v = apply_rule<RULE, M>(src, base + c, W, gr, c, a, ra);
                         dst[base + c] = v;
-                        if (converge && lr >= 0 && lr < nr) s_mine += fabs((double)v);
+                        if (converge && lr >= 0 && lr < nr) sum2_add(sh, sl, fabsf(v), 0.0f);
                     }
                 }
             }
@@ -190,7 +217,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
         }
         done += Kb;
         if (converge) {
-            const double t = block_sum(s_mine, scratch);
+            const double t = block_sum2(sh, sl, scratch);
             if (tid == 0) part[par] = t;
         }
         // first H rows to the neighbour above (its bottom inbox), last H rows
@@ -208,14 +235,15 @@ __global__ void __launch_bounds__(kCThreads, 1)
         }
         barrier();
         if (converge) {
-            double s_new = 0.0;
-            for (int k = 0; k < a.nctas; k++) s_new += part_of(k, par);
-            // r < tol without a division (FP64 division is slow here); r
-            // itself is formed once, by the thread that reports it
-            stop = s_old > 0.0 && fabs(s_new - s_old) < tol * s_old;
-            if ((stop || done >= nt) && rank == 0 && tid == 0)
+            if (tid == 0) {
+                double s_new = 0.0;
+                for (int k = 0; k < a.nctas; k++) s_new += part_of(k, par);
                 r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
-            s_old = s_new;
+                *flag = r_last < tol ? 1 : 0;
+                s_old = s_new;
+            }
+            __syncthreads();
+            stop = *flag != 0;
         }
         if (a.nctas > 1 && done < nt && !stop) {
             float *d = buf[cur];
@@ -252,8 +280,9 @@ __global__ void __launch_bounds__(kCThreads, 1)
 
 size_t cluster_smem_bytes(int strip, int halo, int width, int cols)
 {
+    // two buffers, the inboxes, 2 partial sums, 32 warps' (hi, lo), a flag
     return sizeof(float) * (2 * (size_t)(strip + 2 * halo) * width + 4 * (size_t)halo * cols) +
-           sizeof(double) * (2 + 32);
+           sizeof(double) * 2 + sizeof(float) * 64 + 16;
 }
 
 template <int RULE, int M>
