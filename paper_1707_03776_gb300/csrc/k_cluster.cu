@@ -117,10 +117,17 @@ __device__ __forceinline__ double block_sum2(float hi, float lo, float *scratch)
     }
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x == 0) {
-        float h = 0.0f, q = 0.0f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) sum2_add(h, q, scratch[2 * i], scratch[2 * i + 1]);
-        t = (double)h + (double)q;
+    if (w == 0) {
+        // second stage in warp 0: its lanes take the warps' pairs
+        const int nw = (int)(blockDim.x >> 5);
+        hi = l < nw ? scratch[2 * l] : 0.0f;
+        lo = l < nw ? scratch[2 * l + 1] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            sum2_add(hi, lo, oh, ol);
+        }
+        if (l == 0) t = (double)hi + (double)lo;
     }
     __syncthreads();
     return t;
@@ -238,8 +245,11 @@ __global__ void __launch_bounds__(kCThreads, 1)
             if (tid == 0) {
                 double s_new = 0.0;
                 for (int k = 0; k < a.nctas; k++) s_new += part_of(k, par);
-                r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
-                *flag = r_last < tol ? 1 : 0;
+                // r < tol as a product (FP64 division is slow here); r itself
+                // is formed when the loop ends
+                const bool hit = s_old > 0.0 && fabs(s_new - s_old) < tol * s_old;
+                if (hit || done >= nt) r_last = s_old > 0.0 ? fabs(s_new - s_old) / s_old : INFINITY;
+                *flag = hit ? 1 : 0;
                 s_old = s_new;
             }
             __syncthreads();
