@@ -2,7 +2,9 @@
 with checkpointing, behind a torch.autograd.Function.
 
 Forward: the operator of the Seismic Inversion Example run from rest; every
-`checkpoint_every` steps the two wavefield levels are copied aside.
+`checkpoint_every` steps the two wavefield levels are copied aside -- or,
+when the whole history fits in device memory (256^3 x 1500 steps is 100 GB
+of the GPU's 280 GB), every state is kept and nothing is recomputed.
 Backward: the paper's adjoint operator (the same update run backward in time
 with the receiver residual injected, FD_FLAG_REVERSE) sweeps the checkpoint
 segments from last to first; inside each segment the forward states are
@@ -32,14 +34,22 @@ class Shot:
 class Propagator:
     """Device-resident forward and adjoint operators for one grid and shot."""
 
-    def __init__(self, shape, spacing, origin, space_order, shot, nt, dt, checkpoint_every=50, flags=0):
+    def __init__(self, shape, spacing, origin, space_order, shot, nt, dt, checkpoint_every=None, flags=0):
+        """checkpoint_every: k > 0 keeps two states every k steps and
+        recomputes the segments in the backward sweep; 0 keeps the whole
+        forward history in device memory (no recomputation); None picks 0
+        when the history takes at most half the free device memory, else 50."""
         import torch
         self.torch = torch
         self.shape = tuple(int(s) for s in shape)
         self.nt = int(nt)
         self.dt = float(dt)
-        self.k = int(checkpoint_every)
         self.grid = fd.Grid(self.shape, spacing, origin)
+        slot_bytes = 4 * int(np.prod(self.grid.padded_shape))
+        if checkpoint_every is None:
+            free, _ = torch.cuda.mem_get_info()
+            checkpoint_every = 0 if (self.nt + 2) * slot_bytes <= free // 2 else 50
+        self.k = int(checkpoint_every)
         self.m = fd.DenseData("m", self.grid)
         self.eta = fd.DenseData("eta", self.grid)
         self.m.data.fill_(1.0)
@@ -57,12 +67,16 @@ class Propagator:
         self.res = fd.PointData("res", self.grid, shot.rec_coords, self.nt)
         self.adj = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, space_order, self.mu, self.m, self.eta, src=self.res,
                                flags=flags | fd.FD_FLAG_REVERSE)
-        nseg = (self.nt + self.k - 1) // self.k
         ps = self.grid.padded_shape
-        # checkpoint j: the states of times jk-1 and jk-2 (zero for j = 0)
-        self.ckpt = torch.zeros((nseg, 2) + ps, dtype=torch.float32, device="cuda")
-        # segment buffer: states of times jk-2 .. (j+1)k-1
-        self.seg = torch.zeros((self.k + 2,) + ps, dtype=torch.float32, device="cuda")
+        if self.k > 0:
+            nseg = (self.nt + self.k - 1) // self.k
+            # checkpoint j: the states of times jk-1 and jk-2 (zero for j = 0)
+            self.ckpt = torch.zeros((nseg, 2) + ps, dtype=torch.float32, device="cuda")
+            # segment buffer: states of times jk-2 .. (j+1)k-1
+            self.seg = torch.zeros((self.k + 2,) + ps, dtype=torch.float32, device="cuda")
+        else:
+            # the whole history: hist[i] holds the state of time i-1 (-1 .. nt)
+            self.hist = torch.zeros((self.nt + 2,) + ps, dtype=torch.float32, device="cuda")
         self.grad = fd.DenseData("grad", self.grid)
 
     def set_damping(self, eta):
@@ -83,7 +97,16 @@ class Propagator:
             op.bind("eta", self.eta)
 
     def forward(self):
-        """Forward run from rest with checkpoints; returns the device traces."""
+        """Forward run from rest with checkpoints (or the whole history);
+        returns the device traces."""
+        if self.k == 0:
+            hist = self.hist
+            hist[0].zero_()
+            hist[1].zero_()
+            for n in range(self.nt):
+                fd.fd_operator_step(self.fwd.handle, n, self.dt, hist[n + 1].data_ptr(), hist[n].data_ptr(),
+                                    hist[n + 2].data_ptr())
+            return self.rec.data[:, : self.rec.npoint]
         for s in self.u.slots:
             s.zero_()
         self.ckpt[0].zero_()
@@ -111,6 +134,15 @@ class Propagator:
         g = self.grid.handle
         stream = torch.cuda.current_stream().cuda_stream
         scale = -1.0 / (self.dt * self.dt)
+        if self.k == 0:
+            hist = self.hist
+            for n in range(self.nt - 1, -1, -1):
+                self.adj.apply(n, 1, self.dt)
+                if n >= 1:
+                    fd.fd_imaging_accumulate(g, scale, self.mu.slots[n % 2].data_ptr(), hist[n + 1].data_ptr(),
+                                             hist[n].data_ptr(), hist[n - 1].data_ptr(),
+                                             self.grad.slots[0].data_ptr(), stream)
+            return self.grad.data
         k = self.k
         seg = self.seg
         for j in range(self.ckpt.shape[0] - 1, -1, -1):

@@ -64,11 +64,14 @@ def test_gradient_matches_oracle():
 
 def test_checkpointing_is_exact():
     """Recomputing segments from checkpoints reproduces the stored-history
-    gradient bit for bit (the same kernel on the same inputs)."""
+    gradient bit for bit (the same kernel on the same inputs), and so does
+    keeping the whole forward history (checkpoint_every=0)."""
     case = _case(seed=5, nt=90)
     _, g1 = _gpu_gradient(case, 90)
     _, g2 = _gpu_gradient(case, 17)
     np.testing.assert_array_equal(g1, g2)
+    J0, g0 = _gpu_gradient(case, 0)
+    np.testing.assert_array_equal(g1, g0)
 
 
 def test_plain_kernels_agree():
