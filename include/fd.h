@@ -406,6 +406,18 @@ fd_status fd_cnn_pack_weights(const float *w, int cin, int cout, int flip, void 
  * activations.  shape: 3 int64. */
 fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const void *frag, const float *bias, int cout,
                         int relu, const void *mask, void *y, int y_fp32, void *cuda_stream);
+/* The same convolution on the 5th-generation tensor cores (tcgen05.mma with
+ * tensor-memory accumulators, TMA-loaded planes): results equal
+ * fd_cnn_conv3d's; weights packed by fd_cnn_pack_weights_tc into 27 * 512
+ * bytes ([tap][2 halves][16 out][8 in] BF16).  x, y and mask must be 16-byte
+ * aligned (FD_ERR_LAYOUT).  status: a device int the kernel sets to
+ * FD_ERR_TIMEOUT if one of its bounded waits gave up (caller clears it).
+ * With 16 output channels the tensor core is bound by its shared-memory reads
+ * of the activation tile and is not faster than fd_cnn_conv3d, which the
+ * closure uses; this path is kept for comparison. */
+fd_status fd_cnn_pack_weights_tc(const float *w, int cin, int cout, int flip, void *frag, void *cuda_stream);
+fd_status fd_cnn_conv3d_tc(const int64_t *shape, const void *x, const void *frag, const float *bias, int cout,
+                           int relu, const void *mask, void *y, int y_fp32, int *status, void *cuda_stream);
 /* Weight and bias gradients of a layer, accumulated (+=) into FP32
  * gw[27][cin][cout] and gb[cout]: gw[t][c][o] += sum_p x[p + offset_t][c]
  * gy[p][o]. */

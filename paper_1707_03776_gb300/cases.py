@@ -12,6 +12,7 @@ the device at most.
              shot (256^3 SO8, 100 steps, checkpoints every 10 steps)
   diffusion  the 2D diffusion cluster kernel (256^2 ring, 500 steps per run)
   conv       the closure network's forward convolutions (160^3 activations)
+  conv_tc    the same on the tcgen05 kernel
   wgrad      the closure network's weight-gradient kernel (96^3)
 """
 import argparse
@@ -113,6 +114,21 @@ def case_conv(args):
     _sync()
 
 
+def case_conv_tc(args):
+    import torch
+    from . import closure
+    net = closure.ClosureNet(seed=0, rho=1e-3)
+    shape = (args.n,) * 3
+    ws = closure.Workspace(shape)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    ws.h[0].copy_(torch.randn(ws.h[0].shape, generator=g, device="cuda").to(torch.bfloat16))
+    ws.h[0][:, 6:].zero_()
+    st = torch.cuda.current_stream().cuda_stream
+    for _ in range(args.reps):
+        closure.network_forward(net, ws, st, tensor_memory=True)
+    _sync()
+
+
 def case_wgrad(args):
     import torch
     from . import closure, fd
@@ -130,7 +146,7 @@ def case_wgrad(args):
 
 
 CASES = {"acoustic": case_acoustic, "batch": case_batch, "gradient": case_gradient, "diffusion": case_diffusion,
-         "conv": case_conv, "wgrad": case_wgrad}
+         "conv": case_conv, "conv_tc": case_conv_tc, "wgrad": case_wgrad}
 
 
 def main(argv=None):
@@ -146,7 +162,7 @@ def main(argv=None):
     p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel")
     args = p.parse_args(argv)
     defaults = {"acoustic": (512, 10), "batch": (None, 10), "gradient": (256, 100), "diffusion": (256, 500),
-                "conv": (160, None), "wgrad": (96, None)}
+                "conv": (160, None), "conv_tc": (160, None), "wgrad": (96, None)}
     n, nt = defaults[args.case]
     args.n = args.n or n
     args.nt = args.nt or nt

@@ -67,6 +67,8 @@ class ClosureNet:
                        for i in range(NLAYER)]
         self.rho = float(rho)
         self.vref = 3500.0
+        self.frag_tc = None  # tcgen05 operand layout, packed on first use
+        self.tc_status = None
         self.pack()
 
     def weight(self, li):
@@ -79,6 +81,7 @@ class ClosureNet:
 
     def pack(self):
         st = _stream()
+        self.frag_tc = None
         for li in range(NLAYER):
             cin, cout = CHANNELS[li], CHANNELS[li + 1]
             fd.fd_cnn_pack_weights(self.weight(li), cin, cout, 0, self.frag[li], st)
@@ -116,14 +119,26 @@ class Workspace:
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
 
-def network_forward(net, ws, stream=None):
-    """ws.h[0] (features) -> ws.out (FP32, one channel)."""
+def network_forward(net, ws, stream=None, tensor_memory=False):
+    """ws.h[0] (features) -> ws.out (FP32, one channel).  tensor_memory=True
+    runs the layers on the tcgen05 kernel instead (same results; slower with
+    16 channels, kept for comparison)."""
     st = stream or _stream()
+    if tensor_memory and net.frag_tc is None:
+        import torch
+        net.frag_tc = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
+        net.tc_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for li in range(NLAYER):
+            fd.fd_cnn_pack_weights_tc(net.weight(li), CHANNELS[li], CHANNELS[li + 1], 0, net.frag_tc[li], st)
     for li in range(NLAYER):
         last = li == NLAYER - 1
         y = ws.out if last else ws.h[li + 1]
-        fd.fd_cnn_conv3d(ws.shape, ws.h[li], net.frag[li], None, CHANNELS[li + 1], 0 if last else 1, None, y,
-                         1 if last else 0, st)
+        if tensor_memory:
+            fd.fd_cnn_conv3d_tc(ws.shape, ws.h[li], net.frag_tc[li], None, CHANNELS[li + 1], 0 if last else 1, None,
+                                y, 1 if last else 0, net.tc_status, st)
+        else:
+            fd.fd_cnn_conv3d(ws.shape, ws.h[li], net.frag[li], None, CHANNELS[li + 1], 0 if last else 1, None, y,
+                             1 if last else 0, st)
 
 
 def network_backward(net, ws, stream=None):

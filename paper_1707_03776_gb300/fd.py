@@ -94,6 +94,9 @@ _SIGNATURES = [
     ("fd_cnn_pack_weights", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     ("fd_cnn_conv3d", ctypes.c_int, [_c_i64p, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
                                      _vp]),
+    ("fd_cnn_pack_weights_tc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    ("fd_cnn_conv3d_tc", ctypes.c_int, [_c_i64p, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
+                                        _vp, _vp]),
     ("fd_cnn_conv3d_wgrad", ctypes.c_int, [_c_i64p, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     ("fd_cnn_features", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_uint64, _vp, _vp]),
@@ -370,6 +373,16 @@ def fd_cnn_conv3d(shape, x, frag, bias, cout, relu, mask, y, y_fp32, stream=0):
     shp = _i64(shape)
     _check(lib().fd_cnn_conv3d(shp.ctypes.data_as(_c_i64p), _ptr(x), _ptr(frag), _ptr(bias), int(cout), int(relu),
                                _ptr(mask), _ptr(y), int(y_fp32), int(stream) or None))
+
+
+def fd_cnn_pack_weights_tc(w, cin, cout, flip, frag, stream=0):
+    _check(lib().fd_cnn_pack_weights_tc(_ptr(w), int(cin), int(cout), int(flip), _ptr(frag), int(stream) or None))
+
+
+def fd_cnn_conv3d_tc(shape, x, frag, bias, cout, relu, mask, y, y_fp32, status, stream=0):
+    shp = _i64(shape)
+    _check(lib().fd_cnn_conv3d_tc(shp.ctypes.data_as(_c_i64p), _ptr(x), _ptr(frag), _ptr(bias), int(cout),
+                                  int(relu), _ptr(mask), _ptr(y), int(y_fp32), _ptr(status), int(stream) or None))
 
 
 def fd_cnn_conv3d_wgrad(shape, x, gy, cin, cout, gw, gb, stream=0):

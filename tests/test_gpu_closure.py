@@ -357,3 +357,53 @@ def test_training_lowers_loss_and_trace_error():
     plain = closure.trace_error(op.run(learned=False).cpu().numpy(), ref)
     learned = closure.trace_error(op.run(learned=True).cpu().numpy(), ref)
     assert np.isfinite(learned) and learned < 0.85 * plain, (learned, plain)
+
+
+@pytest.mark.parametrize("cin,cout,relu,mask,flip,f32", [(6, 16, True, False, 0, False), (16, 16, False, True, 0, False),
+                                                        (16, 5, True, True, 0, False), (16, 1, False, False, 0, True),
+                                                        (16, 16, False, True, 1, False), (6, 16, False, False, 1, False)])
+def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32):
+    """The tcgen05 kernel gives the mma.sync kernel's results bit for bit
+    (both accumulate each tap's 16-term products in FP32 in the same order)
+    and so the oracle parity; shapes ragged against its 2-row x 128-point
+    tiles and 16-plane chunks."""
+    torch = _torch()
+    fd = _fd()
+    st = torch.cuda.current_stream().cuda_stream
+    shape = (19, 7, 150)
+    g = np.random.default_rng(400 + cin + cout + flip)
+    nin = cout if flip else cin  # channels the convolution reads
+    nout = cin if flip else cout
+    x = _pad16(g.standard_normal(shape + (nin,)).astype(np.float32))
+    w = (g.standard_normal((27, cin, cout)) / np.sqrt(27 * nin)).astype(np.float32)
+    xt, xr = _bf16_acts(x)
+    mt, mr = _bf16_acts(g.standard_normal(shape + (16,)).astype(np.float32))
+    wd = torch.from_numpy(w).cuda()
+    frag = torch.zeros(27 * 512, dtype=torch.uint8, device="cuda")
+    frag_tc = torch.zeros(27 * 512, dtype=torch.uint8, device="cuda")
+    fd.fd_cnn_pack_weights(wd, cin, cout, flip, frag, st)
+    fd.fd_cnn_pack_weights_tc(wd, cin, cout, flip, frag_tc, st)
+    n = xt.shape[0]
+    mk = mt if mask else None
+    if f32:
+        y1 = torch.zeros(n, dtype=torch.float32, device="cuda")
+        y2 = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    else:
+        y1 = torch.zeros((n, 16), dtype=torch.bfloat16, device="cuda")
+        y2 = torch.full((n, 16), float("nan"), dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fd.fd_cnn_conv3d(shape, xt, frag, None, nout, int(relu), mk, y1, int(f32), st)
+    fd.fd_cnn_conv3d_tc(shape, xt, frag_tc, None, nout, int(relu), mk, y2, int(f32), status, st)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    np.testing.assert_array_equal(y2.float().cpu().numpy(), y1.float().cpu().numpy())
+    wr = cnn.bf16_round(w).astype(np.float64)
+    ref = cnn.conv3d_grad_input(xr[..., :cout], wr) if flip else cnn.conv3d(xr[..., :cin], wr, np.zeros(cout))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    if mask:
+        ref = ref * (mr[..., :nout] > 0)
+    got = y2.float().cpu().numpy().reshape(shape + ((16,) if not f32 else ()))
+    got = got[..., 0] if f32 else got[..., :nout]
+    ref = ref[..., 0] if f32 else ref
+    assert np.abs(got - ref).max() <= 2.0 ** -8 * np.abs(ref).max() + 1e-4 * np.abs(ref).max()
