@@ -403,7 +403,9 @@ def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32):
         ref = np.maximum(ref, 0.0)
     if mask:
         ref = ref * (mr[..., :nout] > 0)
-    got = y2.float().cpu().numpy().reshape(shape + ((16,) if not f32 else ()))
-    got = got[..., 0] if f32 else got[..., :nout]
-    ref = ref[..., 0] if f32 else ref
+    if f32:
+        got = y2.cpu().numpy().reshape(shape)
+        ref = ref[..., 0]
+    else:
+        got = y2.float().cpu().numpy().reshape(shape + (16,))[..., :nout]
     assert np.abs(got - ref).max() <= 2.0 ** -8 * np.abs(ref).max() + 1e-4 * np.abs(ref).max()
