@@ -63,6 +63,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world):
+    """The largest of every rank's value (all ranks receive it): the job's
+    time is its slowest replica's.  Uses the default process group when
+    world > 1 (a CUDA tensor under NCCL, a CPU one under gloo)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_step, steps, world, seconds):
+    """GPts/s of the whole job: every rank runs its own replica (weak
+    scaling), so the points of all ranks over the slowest rank's time."""
+    return points_per_step * steps * world / seconds / 1e9
+
+
 def workload_name(n, so, nt):
     return "acoustic3d_%d^3_so%d_nt%d_1src_101x101rec_sponge40" % (n, so, nt)
 
@@ -667,12 +687,9 @@ def run_ours(args):
     launches = op.launches - launches0
     op.sync()
     k_ms, k_n = op.profile_read()
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world)
     pts = float(args.n) ** 3 * args.nt
-    value = pts * args.steps * world / (ms_max * 1e-3) / 1e9
+    value = whole_job_rate(pts, args.steps, world, ms_max * 1e-3)
 
     # receivers must hold a finite, non-trivial shot record
     rec = model.rec.data[:, : model.rec.npoint]
@@ -689,10 +706,7 @@ def run_ours(args):
             out = model.forward(m_h, eta_h, src_h, cfg["dt"])
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        el_t = torch.tensor([el], device="cuda")
-        if world > 1:
-            dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": pts * e_steps * world / float(el_t.item()) / 1e9, "unit": "GPts/s",
+        e2e = {"value": whole_job_rate(pts, e_steps, world, max_over_ranks(el, world)), "unit": "GPts/s",
                "h2d_bytes_per_step": model.h2d_bytes(), "d2h_bytes_per_step": model.d2h_bytes(),
                "steps": e_steps, "api": "AcousticModel.forward (host pinned m, eta, wavelet -> host traces)"}
         assert out.shape[0] == args.nt
