@@ -155,8 +155,10 @@ typedef struct fd_sparse fd_sparse;
  * surrounding nodes weighted by products of f and 1 - f.  The table is
  * uploaded on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
  * npoint may be 0.
- * Errors: FD_ERR_INVALID_ARG, FD_ERR_OUT_OF_DOMAIN (a point outside
- * [origin, origin + (n-1) h] on some axis), FD_ERR_NOMEM, FD_ERR_CUDA. */
+ * Errors: FD_ERR_INVALID_ARG (also for npoint > 0 on a grid with an axis of
+ * fewer than 2 nodes, which has no interpolation cell), FD_ERR_OUT_OF_DOMAIN
+ * (a point outside [origin, origin + (n-1) h] on some axis), FD_ERR_NOMEM,
+ * FD_ERR_CUDA. */
 fd_status fd_sparse_create(const fd_grid *grid, int npoint, const double *coords,
                            void *dev_trace, int64_t nt, int64_t trace_stride,
                            void *cuda_stream, fd_sparse **out);

@@ -275,6 +275,12 @@ extern "C" fd_status fd_sparse_create(const fd_grid *g, int npoint, const double
         return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: null coordinates or trace");
     if (nt < 0 || (npoint > 0 && trace_stride < npoint))
         return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: need nt >= 0 and trace_stride >= npoint");
+    // the linear-interpolation cell of a point spans nodes i and i+1 on
+    // every axis: an axis of one node has no cell
+    for (int a = 0; a < g->ndim && npoint > 0; a++)
+        if (g->shape[a] < 2)
+            return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: axis %d has %lld node(s); points need >= 2", a,
+                             (long long)g->shape[a]);
     const int ndim = g->ndim;
     int64_t padded[3], st[3];
     layout_of(*g, padded, st);

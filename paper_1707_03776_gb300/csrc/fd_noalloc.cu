@@ -51,6 +51,10 @@ extern "C" fd_status fd_interpolate_noalloc(const fd_grid *g, int npoint, const 
                          "fd_interpolate_noalloc: %d points requested, the static table holds at most %d", npoint,
                          kMaxPoints);
     if (npoint == 0) return FD_OK;
+    for (int a = 0; a < g->ndim; a++)
+        if (g->shape[a] < 2)
+            return set_error(FD_ERR_INVALID_ARG, "fd_interpolate_noalloc: axis %d has %lld node(s); points need >= 2",
+                             a, (long long)g->shape[a]);
     if (!coords || !dev_field || !dev_out)
         return set_error(FD_ERR_INVALID_ARG, "fd_interpolate_noalloc: null pointer");
     const int ndim = g->ndim;

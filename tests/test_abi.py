@@ -135,3 +135,8 @@ def test_sparse_domain_check_before_device(L):
         fd.fd_sparse_create(g, np.array([[2.0, 2.0, 2.0]]), 4096, 10, 0)
     assert e.value.status == fd.FD_ERR_INVALID_ARG
     fd.fd_grid_destroy(g)
+    # grids need 2 nodes per axis (an axis of one node has no interpolation
+    # cell and no stencil)
+    with pytest.raises(fd.FDError) as e:
+        fd.fd_grid_create((8, 1, 10), (2.0, 2.0, 2.0), (0.0, 0.0, 0.0))
+    assert e.value.status == fd.FD_ERR_INVALID_ARG

@@ -214,3 +214,35 @@ def test_tilings_agree_bitwise_and_autotune():
         fd.fd_operator_set_tiling(run.op.handle, 64, 2)
     assert e.value.status == fd.FD_ERR_UNSUPPORTED
     assert fd.fd_operator_get_tiling(run.op.handle)[:2] == (rows, stages)
+
+
+@pytest.mark.parametrize("flags", [0, fd.FD_FLAG_PLAIN_KERNELS], ids=["tiled", "plain"])
+@pytest.mark.parametrize("so,shape", [
+    (2, (2, 2, 2)), (16, (3, 5, 2)), (8, (2, 2, 9)), (4, (2, 70, 3)), (16, (17, 2, 65)),
+    (2, (2, 2)), (16, (2, 40)), (8, (3, 3)),
+])
+def test_degenerate_shapes(so, shape, flags):
+    """The smallest grids (2 nodes per axis), grids thinner than the
+    stencil's half-width and contiguous axes of 2-3 points (TMA boxes almost
+    entirely outside the grid): the zero halo still gives the oracle's
+    result.  A source on the grid's last node and a receiver on its first
+    exercise the interpolation table's clamp."""
+    h = 10.0
+    nd = len(shape)
+    m, eta, dt = _model(shape, h, 0, 2)
+    u = wl.random_field(shape, 30 + so, smooth=0)
+    up = wl.random_field(shape, 40 + so, smooth=0)
+    hi = np.array([(n - 1) * h for n in shape], dtype=np.float64).reshape(1, nd)
+    lo = np.zeros((1, nd))
+    nt = 3
+    src_trace = np.linspace(1.0, 2.0, nt).astype(np.float32).reshape(nt, 1)
+    run = AcousticRun(shape, (h,) * nd, None, so, m, eta, src_coords=hi, src_trace=src_trace, rec_coords=lo,
+                      n_total=nt, flags=flags | fd.FD_FLAG_NO_CFL_CHECK)
+    run.set_state(u, up)
+    run.run(0, nt, dt)
+    got, _ = run.state(nt)
+    ref, _, rec = oracle.acoustic_forward(shape, (h,) * nd, (0,) * nd, so, m, eta, dt, nt, src_coords=hi,
+                                          src_trace=src_trace, rec_coords=lo, u_cur=u.astype(np.float64),
+                                          u_prev=up.astype(np.float64))
+    assert rel_l2(got, ref) <= 1e-5
+    np.testing.assert_allclose(run.rec_trace()[:, 0], rec[:, 0], rtol=1e-5, atol=1e-6 * np.abs(rec).max())
