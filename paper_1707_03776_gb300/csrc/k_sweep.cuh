@@ -93,8 +93,7 @@ __host__ __device__ constexpr int round_up32(int x) { return (x + 31) / 32 * 32;
 __host__ __device__ inline int ring_plane_floats(int box_h) { return round_up32(box_h * kBoxW); }
 
 // Byte offsets of the areas of a tiled CTA's dynamic shared memory: the u^n
-// ring, the aux ring and a zero plane, the mbarriers, the abort flag (16
-// bytes), then src_cap
+// ring, the aux ring, the mbarriers, the abort flag (16 bytes), then src_cap
 // injected corners of the tile and their n0 + 1 per-plane starts.  Both the
 // size a launch requests and the carve in the kernel come from here.
 struct SmemLayout {
@@ -106,8 +105,7 @@ __host__ __device__ inline SmemLayout tma_smem_layout(int M, int P, int rows_max
     const int NU = M + 1 + P, NA = P + 1;
     SmemLayout l;
     l.aux = sizeof(float) * (size_t)NU * ring_plane_floats(rows_max + 2 * M);
-    // the aux ring, then one plane of zeros (the d of undamped planes)
-    l.bars = l.aux + sizeof(float) * (size_t)(NA * 3 + 1) * rows_max * kTileW;
+    l.bars = l.aux + sizeof(float) * (size_t)NA * 3 * rows_max * kTileW;
     l.abort = l.bars + sizeof(unsigned long long) * (size_t)(NU + NA);
     l.src = l.abort + 16;
     l.sstart = l.src + sizeof(SrcEntry) * (size_t)src_cap;
@@ -226,13 +224,6 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
     // for bit: d (u - u^{n-1}) = 0 exactly).  dmask: one bit per plane, set
     // where some node is damped; null = every plane damped.
     auto undamped = [&](int z) { return dmask && !((__ldg(dmask + (z >> 5)) >> (z & 31)) & 1u); };
-    // the compute side keeps the mask word of its current output plane in a
-    // register (reloaded every 32 planes) and reads d through a pointer that
-    // is the zero plane where the tile is undamped
-    const float *zero_plane = aux + NA * 3 * plane_a;
-    for (int q = tid; q < plane_a && dmask; q += blockDim.x) const_cast<float *>(zero_plane)[q] = 0.0f;
-    unsigned dword = 0xffffffffu;
-    int dword_at = -1;
 
     // iteration j: u^n plane z_lo-M+j into ring slot (iu+j) % NU; for j >= 2M
     // the aux of output plane z_lo+j-2M into aux slot (ia+j-2M) % NA
@@ -326,12 +317,8 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
                 const float *pa = aux + ((ia + ja) % NA) * 3 * plane_a + r * kTileW + 4 * qc;
                 const float4 um4 = *reinterpret_cast<const float4 *>(pa);
                 const float4 c4 = *reinterpret_cast<const float4 *>(pa + plane_a);
-                if (dmask && (zo >> 5) != dword_at) {
-                    dword_at = zo >> 5;
-                    dword = __ldg(dmask + dword_at);
-                }
-                const float *pd = ((dword >> (zo & 31)) & 1u) ? pa + 2 * plane_a : zero_plane + r * kTileW + 4 * qc;
-                const float4 d4 = *reinterpret_cast<const float4 *>(pd);
+                const float4 d4 = undamped(zo) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                               : *reinterpret_cast<const float4 *>(pa + 2 * plane_a);
                 const float umv[4] = {um4.x, um4.y, um4.z, um4.w};
                 const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
                 const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
