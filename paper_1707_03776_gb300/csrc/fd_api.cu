@@ -654,21 +654,12 @@ static fd_status check_dt(const fd_operator *op, double dt, const char *who)
 // inputs changed.
 static fd_status prepare_coefficients(fd_operator *op, double dt)
 {
-    if (op->kind != FD_ACOUSTIC_LEAPFROG) return FD_OK;
+    if (op->kind != FD_ACOUSTIC_LEAPFROG || op->coef_dt == dt) return FD_OK;
     cudaStream_t st = op->stream;
-    if (op->coef_dt != dt) {
-        FD_CUDA(launch_coefficients(op->geom, op->m->slot[0], op->eta ? op->eta->slot[0] : nullptr, dt, op->c, op->d,
-                                    st),
-                "coefficients");
-        op->launches += 1;
-        op->coef_dt = dt;
-        op->tma.dmask_valid = false;
-    }
-    // the tiled kernel's damping mask follows d and the tiling
-    if (op->tma.ready && !op->tma.dmask_valid) {
-        FD_CUDA(tma_damping_mask(op->tma, st), "damping mask");
-        op->launches += 1;
-    }
+    FD_CUDA(launch_coefficients(op->geom, op->m->slot[0], op->eta ? op->eta->slot[0] : nullptr, dt, op->c, op->d, st),
+            "coefficients");
+    op->launches += 1;
+    op->coef_dt = dt;
     return FD_OK;
 }
 

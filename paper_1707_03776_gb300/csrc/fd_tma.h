@@ -69,13 +69,6 @@ struct TmaPlan {
     void *fused_mem = nullptr;
     bool has_src = false;
     int src_cap = 0;  // injected corners per tile staged in shared memory
-    // damping mask: per tile column one bit per d0 plane, set where d is
-    // nonzero on some node of the tile (library-owned; valid after
-    // tma_damping_mask for the current d)
-    float *d = nullptr;
-    unsigned *dmask = nullptr;
-    int dmask_words = 0;
-    bool dmask_valid = false;
     // tensor maps of buffers other than the two slots (out-of-place steps)
     struct CachedMap {
         const void *ptr;
@@ -101,10 +94,6 @@ void tma_plan_tiling(const TmaPlan &plan, int *rows, int *stages, int *ctas);
 cudaError_t launch_acoustic_tma_buffers(TmaPlan &plan, int M, const Coef &cf, const float *u_cur,
                                         const float *u_prev, float *u_next, int *status,
                                         const float *src_row, cudaStream_t st);
-
-// Recompute the plan's damping mask from d (after the coefficients changed or
-// the tiling was rebuilt); enqueued on st.
-cudaError_t tma_damping_mask(TmaPlan &plan, cudaStream_t st);
 
 // Build the fused source-injection table of the plan (src may be null or
 // empty); leaves has_src false when the per-tile lists do not fit.

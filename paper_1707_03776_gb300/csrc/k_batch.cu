@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
                 nsrc = sd->src_off[it.lo + 1] - s0;
             }
             if (!sweep_column<M, P>(&sd->u_halo[cur], &sd->u_tile[cur ^ 1], &sd->c_tile, &sd->d_tile,
-                                    sd->slot[cur ^ 1], a, cf, it.lo, 0, a.n0, sd->src + s0, nsrc, src_row, nullptr,
-                                    sm, it_u, it_a, status))
+                                    sd->slot[cur ^ 1], a, cf, it.lo, 0, a.n0, sd->src + s0, nsrc, src_row, sm, it_u,
+                                    it_a, status))
                 return;
         } else {
             // rec[n][p] = sum_k w_pk u^n(base_p + off_k), as interpolate_kernel

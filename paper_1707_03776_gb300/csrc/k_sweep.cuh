@@ -192,8 +192,8 @@ template <int M, int P>
 __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
                              const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
                              int tile, int z_lo, int z_hi, const SrcEntry *__restrict__ src_tab, int nsrc,
-                             const float *__restrict__ src_row, const unsigned *__restrict__ dmask,
-                             const SweepSmem &sm, unsigned &it_u, unsigned &it_a, int *status)
+                             const float *__restrict__ src_row, const SweepSmem &sm, unsigned &it_u, unsigned &it_a,
+                             int *status)
 {
     constexpr int NU = M + 1 + P;     // u^n planes alive: M behind the newest, the newest, P in flight
     constexpr int NA = P + 1;         // aux planes (u^{n-1}, c, d)
@@ -217,13 +217,7 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
     unsigned long long *bars = sm.bars;
     const uint32_t bytes_u = (uint32_t)(kBoxW * a.box_h * sizeof(float));
     const uint32_t bytes_a = (uint32_t)(3 * a.rows_max * kTileW * sizeof(float));
-    const uint32_t bytes_a2 = (uint32_t)(2 * a.rows_max * kTileW * sizeof(float));
     const unsigned iu = it_u, ia = it_a;
-    // planes of this column where d = dt eta / m is zero on every node: the
-    // d box is not loaded and the damping term is zero (the same result bit
-    // for bit: d (u - u^{n-1}) = 0 exactly).  dmask: one bit per plane, set
-    // where some node is damped; null = every plane damped.
-    auto undamped = [&](int z) { return dmask && !((__ldg(dmask + (z >> 5)) >> (z & 31)) & 1u); };
 
     // iteration j: u^n plane z_lo-M+j into ring slot (iu+j) % NU; for j >= 2M
     // the aux of output plane z_lo+j-2M into aux slot (ia+j-2M) % NA
@@ -238,11 +232,10 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
             const int sa = (int)((ia + (unsigned)ja) % NA);
             const uint32_t ba = smem_addr(&bars[NU + sa]);
             float *dst = aux + sa * 3 * plane_a;
-            const bool dz = undamped(z_lo + ja);
-            mbar_expect_tx(ba, dz ? bytes_a2 : bytes_a);
+            mbar_expect_tx(ba, bytes_a);
             tma_load_3d(smem_addr(dst), map_um, col0, row0, z_lo + ja, ba);
             tma_load_3d(smem_addr(dst + plane_a), map_c, col0, row0, z_lo + ja, ba);
-            if (!dz) tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, z_lo + ja, ba);
+            tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, z_lo + ja, ba);
         }
     };
     auto wait_u = [&](int j) {
@@ -317,8 +310,7 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
                 const float *pa = aux + ((ia + ja) % NA) * 3 * plane_a + r * kTileW + 4 * qc;
                 const float4 um4 = *reinterpret_cast<const float4 *>(pa);
                 const float4 c4 = *reinterpret_cast<const float4 *>(pa + plane_a);
-                const float4 d4 = undamped(zo) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                               : *reinterpret_cast<const float4 *>(pa + 2 * plane_a);
+                const float4 d4 = *reinterpret_cast<const float4 *>(pa + 2 * plane_a);
                 const float umv[4] = {um4.x, um4.y, um4.z, um4.w};
                 const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
                 const float dv[4] = {d4.x, d4.y, d4.z, d4.w};

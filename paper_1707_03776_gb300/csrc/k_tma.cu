@@ -42,8 +42,7 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
                         const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_d,
                         float *__restrict__ out, const TileArgs a, const Coef cf, int *status,
                         const SrcEntry *__restrict__ src_tab, const int *__restrict__ src_off,
-                        const float *__restrict__ src_row, const int src_cap, const unsigned *__restrict__ dmask,
-                        const int dmask_words)
+                        const float *__restrict__ src_row, const int src_cap)
 {
     // an earlier launch of this operator gave up on a wait: do nothing until
     // the host has read and cleared the status word
@@ -68,32 +67,7 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
     const int nsrc = src_row ? src_off[tile + 1] - s0 : 0;
     unsigned it_u = 0, it_a = 0;
     sweep_column<M, P>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc, src_row,
-                       dmask ? dmask + (long long)tile * dmask_words : nullptr, sm, it_u, it_a, status);
-}
-
-// Bit z of word z/32 of tile column t: some node of the tile on plane z has
-// d != 0.  Grid: (tile columns, ceil(n0/32)); each block decides 32 planes.
-__global__ void damping_mask_kernel(const TileArgs a, const float *__restrict__ d, unsigned *__restrict__ mask,
-                                    int words)
-{
-    const int t = blockIdx.x;
-    const int strip = t / a.k2, tile2 = t - strip * a.k2;
-    const int row0 = (int)((long long)strip * a.n1 / a.k1);
-    const int rows = (int)((long long)(strip + 1) * a.n1 / a.k1) - row0;
-    const int col0 = tile2 * kTileW;
-    const int cols = min(kTileW, a.n2 - col0);
-    unsigned word = 0;
-    for (int i = 0; i < 32; i++) {
-        const int z = blockIdx.y * 32 + i;
-        int any = 0;
-        if (z < a.n0)
-            for (int q = threadIdx.x; q < rows * cols; q += blockDim.x) {
-                const int rr = q / cols, cc = q - rr * cols;
-                any |= d[(long long)z * a.s0 + (long long)(row0 + rr) * a.s1 + col0 + cc] != 0.0f;
-            }
-        if (__syncthreads_or(any)) word |= 1u << i;
-    }
-    if (threadIdx.x == 0) mask[(long long)t * words + blockIdx.y] = word;
+                       sm, it_u, it_a, status);
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -267,14 +241,6 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     plan.src_cap = 0;
     plan.slot[0] = slot[0];
     plan.slot[1] = slot[1];
-    plan.d = d;
-    plan.dmask_valid = false;
-    const int words = (a.n0 + 31) / 32;
-    if (plan.dmask) cudaFree(plan.dmask);  // sized for the previous tiling
-    plan.dmask = nullptr;
-    if (cudaMalloc((void **)&plan.dmask, sizeof(unsigned) * (size_t)words * a.k1 * a.k2) != cudaSuccess)
-        return set_error(FD_ERR_NOMEM, "tiled plan: damping mask");
-    plan.dmask_words = words;
     for (int s = 0; s < 2; s++) {
         fd_status st = encode_3d(&plan.u_halo[s], slot[s], a, kBoxW, a.box_h);
         if (st != FD_OK) return st;
@@ -303,12 +269,6 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
 void tma_plan_release(TmaPlan &plan, cudaStream_t st)
 {
     plan.ready = false;
-    if (plan.dmask) {
-        cudaStreamSynchronize(st);
-        cudaFree(plan.dmask);
-    }
-    plan.dmask = nullptr;
-    plan.dmask_valid = false;
     if (plan.fused_mem) {
         cudaStreamSynchronize(st);
         cudaFree(plan.fused_mem);
@@ -402,18 +362,6 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
     return FD_OK;
 }
 
-cudaError_t tma_damping_mask(TmaPlan &plan, cudaStream_t st)
-{
-    plan.dmask_valid = false;
-    if (!plan.ready || !plan.dmask || !plan.d) return cudaSuccess;
-    const TileArgs &a = plan.args;
-    damping_mask_kernel<<<dim3((unsigned)(a.k1 * a.k2), (unsigned)plan.dmask_words), 256, 0, st>>>(
-        a, plan.d, plan.dmask, plan.dmask_words);
-    const cudaError_t e = cudaGetLastError();
-    plan.dmask_valid = e == cudaSuccess;
-    return e;
-}
-
 void tma_plan_tiling(const TmaPlan &plan, int *rows, int *stages, int *ctas)
 {
     *rows = plan.ready ? plan.args.rows_max : 0;
@@ -434,8 +382,7 @@ static cudaError_t launch_maps(const TmaPlan &plan, int M, const Coef &cf, const
     case MM * 8 + PP:                                                                                     \
         acoustic_tma_kernel<MM, PP><<<grid, block, plan.smem, st>>>(                                      \
             map_cur, map_prev, plan.c_tile, plan.d_tile, out, plan.args, cf, status, plan.fused.src,      \
-            plan.fused.src_off, srow, plan.src_cap, plan.dmask_valid ? plan.dmask : nullptr,              \
-            plan.dmask_words);                                                                            \
+            plan.fused.src_off, srow, plan.src_cap);                                                      \
         break;
 #define CASES(MM) CASE(MM, 2) CASE(MM, 3) CASE(MM, 4)
         CASES(1) CASES(2) CASES(3) CASES(4) CASES(5) CASES(6) CASES(7) CASES(8)
