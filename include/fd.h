@@ -405,7 +405,8 @@ fd_status fd_cnn_pack_weights(const float *w, int cin, int cout, int flip, void 
 /* One layer: y = relu?(conv(x, frag) + bias) [* (mask > 0)]; bias (FP32,
  * cout) may be NULL; mask (BF16 activations) may be NULL.  y_fp32 = 1 writes
  * a single linear channel as FP32 [n0*n1*n2] (cout must be 1), else BF16
- * activations.  shape: 3 int64. */
+ * activations.  shape: 3 int64.  x must be 16-byte, frag 8-byte, y and mask
+ * 4-byte aligned (FD_ERR_LAYOUT). */
 fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const void *frag, const float *bias, int cout,
                         int relu, const void *mask, void *y, int y_fp32, void *cuda_stream);
 /* The same convolution on the 5th-generation tensor cores (tcgen05.mma with

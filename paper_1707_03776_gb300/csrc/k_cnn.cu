@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 
 #include "fd_internal.h"
@@ -489,6 +490,9 @@ extern "C" fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const vo
     fd_status s = cnn_dims(3, shape, &d);
     if (s != FD_OK) return s;
     if (!x || !frag || !y || cout < 1 || cout > 16) return set_error(FD_ERR_INVALID_ARG, "fd_cnn_conv3d: bad arguments");
+    // 16-byte copies of the input points, paired BF16 stores and mask loads
+    if (((uintptr_t)x & 15) || ((uintptr_t)frag & 7) || ((uintptr_t)y & 3) || ((uintptr_t)mask & 3))
+        return set_error(FD_ERR_LAYOUT, "fd_cnn_conv3d: x must be 16-byte, frag 8-byte, y and mask 4-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     const __nv_bfloat16 *xb = (const __nv_bfloat16 *)x;
     const __nv_bfloat16 *mk = (const __nv_bfloat16 *)mask;
@@ -534,6 +538,7 @@ extern "C" fd_status fd_cnn_features(const fd_grid *grid, const float *u, const 
     if (!grid || grid->ndim != 3 || !u || !u_prev || !m || !x || !(scale > 0) || !(vref > 0) ||
         !(noise >= 0))
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_features: bad arguments");
+    if ((uintptr_t)x & 3) return set_error(FD_ERR_LAYOUT, "fd_cnn_features: x must be 4-byte aligned");
     const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     features_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
@@ -575,6 +580,7 @@ extern "C" fd_status fd_cnn_mse_grad(const fd_grid *grid, const float *pred, con
 {
     if (!grid || grid->ndim != 3 || !pred || !target || !gy || !loss || !(scale > 0))
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_mse_grad: bad arguments");
+    if ((uintptr_t)gy & 3) return set_error(FD_ERR_LAYOUT, "fd_cnn_mse_grad: gy must be 4-byte aligned");
     const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     mse_grad_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(

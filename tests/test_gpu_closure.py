@@ -409,3 +409,17 @@ def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32):
     else:
         got = y2.float().cpu().numpy().reshape(shape + (16,))[..., :nout]
     assert np.abs(got - ref).max() <= 2.0 ** -8 * np.abs(ref).max() + 1e-4 * np.abs(ref).max()
+
+
+def test_conv3d_rejects_misaligned_buffers():
+    """The 16-byte input copies need a 16-byte aligned x: checked on the host."""
+    torch = _torch()
+    fd = _fd()
+    st = torch.cuda.current_stream().cuda_stream
+    shape = (4, 4, 4)
+    buf = torch.zeros((64 * 16 + 8,), dtype=torch.bfloat16, device="cuda")
+    frag = torch.zeros(27 * 512, dtype=torch.uint8, device="cuda")
+    y = torch.zeros((64, 16), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(fd.FDError) as e:
+        fd.fd_cnn_conv3d(shape, buf.data_ptr() + 2, frag, None, 16, 0, None, y, 0, st)
+    assert e.value.status == fd.FD_ERR_LAYOUT
