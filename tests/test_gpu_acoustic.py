@@ -246,3 +246,25 @@ def test_degenerate_shapes(so, shape, flags):
                                           u_prev=up.astype(np.float64))
     assert rel_l2(got, ref) <= 1e-5
     np.testing.assert_allclose(run.rec_trace()[:, 0], rec[:, 0], rtol=1e-5, atol=1e-6 * np.abs(rec).max())
+
+
+@pytest.mark.parametrize("so", [4, 8, 16])
+def test_full_run_128(so):
+    """The 512^3 benchmark's recipe at 128^3 x 300 steps (40-cell-strength
+    sponge of 16 cells, 33 x 33 receivers): receiver traces and the final
+    field against the FP64 oracle's full run, relative L2 <= 1e-4; the
+    planner's tiling (d0 chunks at this size) as the bench uses it."""
+    cfg = wl.acoustic_config(n=128, space_order=so, nt=300, sponge=16, nrec_side=33)
+    run = AcousticRun(cfg["shape"], cfg["spacing"], cfg["origin"], so, cfg["m"], cfg["eta"],
+                      cfg["src_coords"], cfg["src_trace"], cfg["rec_coords"], cfg["nt"])
+    rows, stages, ctas = fd.fd_operator_get_tiling(run.op.handle)
+    assert ctas >= 152  # the columns alone would leave SMs idle: d0 chunks
+    run.run(0, cfg["nt"], cfg["dt"])
+    rec = run.rec_trace()
+    u_end, _ = run.state(cfg["nt"])
+    ou, _, orec = oracle.acoustic_forward(cfg["shape"], cfg["spacing"], cfg["origin"], so, cfg["m"],
+                                          cfg["eta"], cfg["dt"], cfg["nt"], src_coords=cfg["src_coords"],
+                                          src_trace=cfg["src_trace"], rec_coords=cfg["rec_coords"])
+    assert np.abs(orec).max() > 0
+    assert rel_l2(rec, orec) <= TRACE_TOL
+    assert rel_l2(u_end, ou) <= TRACE_TOL
