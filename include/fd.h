@@ -283,6 +283,14 @@ fd_status fd_operator_set_time_block(fd_operator *op, int k);
  * when the operator runs per-step kernels). */
 fd_status fd_operator_get_time_block(const fd_operator *op, int *k, int *ctas);
 
+/* Test hook of the failure path: with plane >= 0, the tiled kernel's first
+ * tile never receives the copy of u^n plane `plane` (its barrier is armed,
+ * the copy not issued), so that CTA's bounded wait gives up after ~2 s,
+ * records FD_ERR_TIMEOUT, drains its copies and returns; later launches do
+ * nothing until fd_operator_sync reports and clears the status.  -1 turns it
+ * off.  Errors: FD_ERR_UNSUPPORTED when the operator has no tiled kernel. */
+fd_status fd_operator_debug_stall(fd_operator *op, int plane);
+
 /* Wait for the operator's stream and report any deferred device error:
  * FD_ERR_CUDA for a failed launch or kernel, FD_ERR_TIMEOUT when a kernel's
  * bounded wait gave up (the status word is then cleared). */

@@ -887,6 +887,15 @@ extern "C" fd_status fd_imaging_accumulate(const fd_grid *g, double scale, const
     return FD_OK;
 }
 
+extern "C" fd_status fd_operator_debug_stall(fd_operator *op, int plane)
+{
+    if (!op || plane < -1) return set_error(FD_ERR_INVALID_ARG, "fd_operator_debug_stall: bad arguments");
+    if (!op->tma.ready) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_debug_stall: no tiled kernel");
+    op->tma.stall_plane = plane;
+    op->tma.args.stall_plane = plane;
+    return FD_OK;
+}
+
 extern "C" fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stages)
 {
     if (!op || rows < 0 || stages < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_set_tiling: bad arguments");

@@ -21,6 +21,7 @@ struct TileArgs {
     long long s0, s1;    // element strides of d0 and d1
     int k1, k2;          // tiles along d1 (balanced strips) and d2 (64 wide)
     int kz;              // chunks of d0 (balanced), each swept by its own CTA
+    int stall_plane;     // test hook: tile 0 never receives this u^n plane (-1: off)
     int rows_max;        // tallest strip
     int box_h;           // rows of a haloed tile: rows_max + 2M
 };
@@ -53,6 +54,7 @@ struct TmaPlan {
     bool ready = false;
     int force_rows = 0;    // > 0: tile height chosen by the caller (autotuner)
     int force_stages = 0;  // > 0: prefetch depth chosen by the caller
+    int stall_plane = -1;  // test hook (TileArgs::stall_plane), kept across rebuilds
     int kind = 0;
     int M = 0;
     int stages = 0;      // prefetch depth P

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kUThreads, 2)
     auto wait_plane = [&](int z) {
         const int slot = ((z % kURing) + kURing) % kURing;
         const bool r = mbar_wait_bounded(smem_addr(&bars[slot]), waited_full[slot] & 1u);
-        waited_full[slot]++;
+        if (r) waited_full[slot]++;  // a copy that did not land is still owed
         return r;
     };
     if (tid == 0) {
@@ -272,12 +272,17 @@ __global__ void __launch_bounds__(kUThreads, 2)
         if (!ok) *abort_flag = 1;
     }
     if (ok && !*abort_flag && z1 > z0) epilogue(z1 - 1);
-    if (!ok || *abort_flag) {
+    // after a wait gave up, every barrier still owed is waited on under one
+    // shared deadline, so one that never completes does not stop the drain
+    // short of the others
+    const bool aborted = !ok || *abort_flag;
+    const unsigned long long deadline = global_ns() + kWaitLimitNs;
+    if (aborted) {
         if (tid == 0) atomicExch(status, (int)FD_ERR_TIMEOUT);
         for (int b = 0; b < 2; b++) {
             const unsigned owed = (unsigned)((issued_planes + (b == 0 ? 1 : 0)) / 2);
             while (waited[b] < owed) {
-                if (!mbar_wait_bounded(smem_addr(&bars[kURing + b]), waited[b] & 1u)) break;
+                if (!mbar_wait_until(smem_addr(&bars[kURing + b]), waited[b] & 1u, deadline)) break;
                 waited[b]++;
             }
         }
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kUThreads, 2)
     if (tid == 0)
         for (int i = 0; i < kURing; i++)
             while (waited_full[i] < loads_into[i]) {
-                if (!mbar_wait_bounded(smem_addr(&bars[i]), waited_full[i] & 1u)) break;
+                if (!mbar_wait_until(smem_addr(&bars[i]), waited_full[i] & 1u, deadline)) break;
                 waited_full[i]++;
             }
     tc_fence_before();

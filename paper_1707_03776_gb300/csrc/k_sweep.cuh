@@ -62,6 +62,15 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Wait for phase `parity` of a barrier until the globaltimer passes
+// `deadline` (a barrier that has already completed returns at once).
+__device__ __forceinline__ bool mbar_wait_until(uint32_t bar, uint32_t parity, unsigned long long deadline)
+{
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() > deadline) return false;
+    return true;
+}
+
 // Wait for phase `parity` of a barrier, giving up after kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 {
@@ -226,7 +235,10 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
         const int su = (int)(gu % NU);
         const uint32_t bu = smem_addr(&bars[su]);
         mbar_expect_tx(bu, bytes_u);
-        tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, z_lo - M + j, bu);
+        // the stall hook arms the barrier but never issues the copy, so the
+        // wait for this plane runs out (the failure path under test)
+        if (a.stall_plane < 0 || tile != 0 || z_lo - M + j != a.stall_plane)
+            tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, z_lo - M + j, bu);
         if (j >= 2 * M) {
             const int ja = j - 2 * M;
             const int sa = (int)((ia + (unsigned)ja) % NA);
@@ -372,13 +384,20 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
 
     if (stop) {
         // a wait gave up: record it, then drain this CTA's copies still in
-        // flight (issued up to min(j+P, J-1)) before leaving
+        // flight (issued up to min(j+P, J-1)) before leaving.  Every barrier
+        // is waited on, under one shared deadline, so that a copy that never
+        // lands does not stop the drain short of the ones behind it.
         if (tid == 0) {
             atomicExch(status, (int)FD_ERR_TIMEOUT);
+            const unsigned long long deadline = global_ns() + kWaitLimitNs;
             const int last = (j + P < J) ? j + P : J - 1;
             for (int i = j; i <= last; i++) {
-                if (!wait_u(i)) break;
-                if (i >= 2 * M && !wait_a(i - 2 * M)) break;
+                const unsigned gu = iu + (unsigned)i;
+                mbar_wait_until(smem_addr(&bars[gu % NU]), (uint32_t)((gu / NU) & 1), deadline);
+                if (i >= 2 * M) {
+                    const unsigned ga = ia + (unsigned)(i - 2 * M);
+                    mbar_wait_until(smem_addr(&bars[NU + ga % NA]), (uint32_t)((ga / NA) & 1), deadline);
+                }
             }
         }
         __syncthreads();

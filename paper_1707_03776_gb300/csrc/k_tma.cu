@@ -212,6 +212,7 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     if (best_k1 < 0) return FD_OK;  // tiles do not fit: plain kernels
     a.k1 = best_k1;
     a.kz = best_kz;
+    a.stall_plane = plan.stall_plane;
     a.rows_max = (a.n1 + a.k1 - 1) / a.k1;
     a.box_h = a.rows_max + 2 * M;
 

@@ -109,6 +109,7 @@ _SIGNATURES = [
                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     ("fd_operator_set_time_block", ctypes.c_int, [_vp, ctypes.c_int]),
     ("fd_operator_get_time_block", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("fd_operator_debug_stall", ctypes.c_int, [_vp, ctypes.c_int]),
     ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -348,6 +349,10 @@ def fd_operator_converge(op, t0, max_iter, tol):
     r = ctypes.c_double(0.0)
     _check(lib().fd_operator_converge(op, int(t0), int(max_iter), float(tol), ctypes.byref(it), ctypes.byref(r)))
     return int(it.value), float(r.value)
+
+
+def fd_operator_debug_stall(op, plane):
+    _check(lib().fd_operator_debug_stall(op, int(plane)))
 
 
 def fd_operator_set_time_block(op, k):

@@ -268,3 +268,32 @@ def test_full_run_128(so):
     assert np.abs(orec).max() > 0
     assert rel_l2(rec, orec) <= TRACE_TOL
     assert rel_l2(u_end, ou) <= TRACE_TOL
+
+
+def test_bounded_wait_gives_up_and_reports():
+    """The failure path on the GPU without a fault: the stall hook arms one
+    tile's barrier for a u^n plane whose copy is never issued, so that CTA's
+    bounded wait (2 s) runs out; it records FD_ERR_TIMEOUT, drains the copies
+    it did issue (one shared 2 s deadline) and returns, the host reads the status at sync, and the next run (hook
+    off) is correct again."""
+    import time
+    cfg = wl.acoustic_config(n=40, space_order=8, nt=6, sponge=4, nrec_side=3)
+    args = (cfg["shape"], cfg["spacing"], cfg["origin"], 8, cfg["m"], cfg["eta"], cfg["src_coords"],
+            cfg["src_trace"], cfg["rec_coords"], cfg["nt"])
+    run = AcousticRun(*args)
+    fd.fd_operator_debug_stall(run.op.handle, 5)
+    t0 = time.perf_counter()
+    run.op.apply(0, 2, cfg["dt"])  # each stalled launch waits ~2 x 2 s
+    with pytest.raises(fd.FDError) as e:
+        run.op.sync()
+    assert e.value.status == fd.FD_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    # the status was cleared by the sync: with the hook off the run is exact
+    fd.fd_operator_debug_stall(run.op.handle, -1)
+    for s in run.u.slots:
+        s.zero_()
+    run.run(0, cfg["nt"], cfg["dt"])
+    ref = AcousticRun(*args)
+    ref.run(0, cfg["nt"], cfg["dt"])
+    np.testing.assert_array_equal(run.state(cfg["nt"])[0], ref.state(cfg["nt"])[0])
+    np.testing.assert_array_equal(run.rec_trace(), ref.rec_trace())
