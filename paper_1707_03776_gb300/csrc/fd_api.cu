@@ -588,7 +588,10 @@ extern "C" fd_status fd_operator_bind(fd_operator *op, const char *name, void *o
         if (!f || f->levels != 2 || !same_shape(f->g, g))
             return set_error(FD_ERR_INVALID_ARG, "fd_operator_bind: u must be a 2-slot field of the same shape");
         op->u = f;
-        return tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+        // the rebuilt plan stages no injected corners until the fused table
+        // is rebuilt for it
+        fd_status s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+        return s != FD_OK ? s : rebuild_fused(op);
     }
     if (n == "m" || n == "eta") {
         if (op->kind != FD_ACOUSTIC_LEAPFROG)

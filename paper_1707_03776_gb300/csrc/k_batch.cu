@@ -79,6 +79,12 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
                 s0 = sd->src_off[it.lo];
                 nsrc = sd->src_off[it.lo + 1] - s0;
             }
+            if (nsrc > src_cap) {
+                // more corners than the launch staged room for (no copies
+                // are in flight between columns)
+                if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
+                return;
+            }
             if (!sweep_column<M, P>(&sd->u_halo[cur], &sd->u_tile[cur ^ 1], &sd->c_tile, &sd->d_tile,
                                     sd->slot[cur ^ 1], a, cf, it.lo, 0, a.n0, sd->src + s0, nsrc, src_row, sm, it_u,
                                     it_a, status))

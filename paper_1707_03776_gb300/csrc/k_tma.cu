@@ -65,6 +65,11 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
     const int z_hi = (int)((long long)(chunk + 1) * a.n0 / a.kz);
     const int s0 = src_row ? src_off[tile] : 0;
     const int nsrc = src_row ? src_off[tile + 1] - s0 : 0;
+    if (nsrc > src_cap) {
+        // more corners than the launch staged room for
+        if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
+        return;
+    }
     unsigned it_u = 0, it_a = 0;
     sweep_column<M, P>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc, src_row,
                        sm, it_u, it_a, status);
