@@ -273,14 +273,25 @@ fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt);
 fd_status fd_operator_converge(fd_operator *op, int64_t t0, int64_t max_iter, double tol, int64_t *iters,
                                double *r_last);
 
-/* Steps between halo exchanges (temporal blocking) of the whole-run cluster
- * kernels of small 2D grids (diffusion, convection, Laplace): k > 0 forces
- * it, 0 restores the planner's choice.  Results do not depend on k.
- * Errors: FD_ERR_UNSUPPORTED when the operator has no cluster path or the
- * strips are thinner than k * half-width rows (the previous value is kept). */
+/* Temporal blocking: the loop blocking of the Devito Loop Engine (Section
+ * "Automated code generation", DLE), which raises data locality to make full
+ * use of the memory bandwidth, carried over to the time loop: more time steps
+ * per pass over memory.
+ * 2D diffusion, convection and Laplace operators: steps between halo
+ * exchanges of the whole-run cluster kernel of small grids; k > 0 forces it,
+ * 0 restores the planner's choice.
+ * 3D acoustic operator: time steps per sweep of the grid, 1 or 2 (0: the
+ * planner's choice, currently 1).  With 2, fd_operator_apply runs pairs of
+ * steps in one cooperative launch (one CTA per tile column, all resident) and
+ * an odd last step alone; it needs SO 4..8 and every source fused into the
+ * tiled kernel.
+ * Results do not depend on k (bitwise).
+ * Errors: FD_ERR_UNSUPPORTED when the operator has no such path or the
+ * blocking does not fit (the previous value is kept). */
 fd_status fd_operator_set_time_block(fd_operator *op, int k);
-/* The cluster path in use: steps per exchange and CTAs in the cluster (both 0
- * when the operator runs per-step kernels). */
+/* The blocking in use: steps per exchange (2D) or per sweep (3D acoustic)
+ * and the CTAs of that path (both 0 when a 2D operator runs per-step
+ * kernels). */
 fd_status fd_operator_get_time_block(const fd_operator *op, int *k, int *ctas);
 
 /* Test hook of the failure path: with plane >= 0, the tiled kernel's first

@@ -52,6 +52,8 @@ struct fd_operator {
     double m_min;          // min(m) over the grid
     int64_t launches;
     fdgb::TmaPlan tma;     // tiled-kernel plan (tensor maps, tiling)
+    fdgb::PairPlan pair;   // two steps per sweep (3D acoustic, SO 4..8)
+    int want_sweep;        // 3D acoustic steps per sweep: 0 planner, 1, 2
     fdgb::ClusterPlan cluster;  // small 2D grids: whole run in one cluster launch
     int want_k;            // forced steps per cluster exchange (0: planner)
     float jac_wr, jac_wc;  // Laplace: weights of the row and column neighbours
@@ -423,7 +425,7 @@ static fd_status reduce_m_min(fd_operator *op)
 
 static fd_status rebuild_fused(fd_operator *op)
 {
-    if (!op->tma.ready) return FD_OK;
+    if (!op->tma.ready && !op->pair.ready) return FD_OK;
     SparseHostView sv;
     const SparseHostView *sp = nullptr;
     if (op->src && op->src->npoint > 0) {
@@ -432,7 +434,21 @@ static fd_status rebuild_fused(fd_operator *op)
         sv.weight = op->src->h_weight.data();
         sp = &sv;
     }
-    return tma_sparse_build(op->tma, sp, op->stream);
+    fd_status s = op->tma.ready ? tma_sparse_build(op->tma, sp, op->stream) : FD_OK;
+    if (s == FD_OK && op->pair.ready) s = pair_sparse_build(op->pair, sp, op->stream);
+    return s;
+}
+
+// Steps per sweep of the acoustic operator: 2 when the two-step kernel is
+// planned, fuses every source and is wanted (forced, or the planner's
+// default), else 1.
+static int acoustic_steps_per_sweep(const fd_operator *op)
+{
+    if (op->kind != FD_ACOUSTIC_LEAPFROG || !op->pair.ready || !op->tma.ready ||
+        (op->flags & FD_FLAG_PLAIN_KERNELS))
+        return 1;
+    if (op->src && op->src->npoint > 0 && !op->pair.has_src) return 1;
+    return op->want_sweep == 2 ? 2 : 1;
 }
 
 static void profile_clear(fd_operator *op)
@@ -479,6 +495,7 @@ static void release(fd_operator *op)
     if (op->d) cudaFreeAsync(op->d, op->stream);
     if (op->status) cudaFreeAsync(op->status, op->stream);
     tma_plan_release(op->tma, op->stream);
+    pair_plan_release(op->pair, op->stream);
     delete op;
 }
 
@@ -539,6 +556,7 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     op->prof_max = 0;
     op->prof_used = 0;
     op->want_k = 0;
+    op->want_sweep = 0;
     op->jac_wr = op->jac_wc = 0.0f;
     op->conv_res = nullptr;
     std::memset(&op->coef, 0, sizeof op->coef);
@@ -571,6 +589,10 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     }
     s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
     if (s != FD_OK) { release(op); return s; }
+    if (op->kind == FD_ACOUSTIC_LEAPFROG && op->tma.ready) {
+        s = pair_plan_build(op->pair, op->so, op->geom, op->u->slot, op->c, op->d);
+        if (s != FD_OK) { release(op); return s; }
+    }
     s = rebuild_fused(op);
     if (s != FD_OK) { release(op); return s; }
     plan_cluster(op);
@@ -591,6 +613,8 @@ extern "C" fd_status fd_operator_bind(fd_operator *op, const char *name, void *o
         // the rebuilt plan stages no injected corners until the fused table
         // is rebuilt for it
         fd_status s = tma_plan_build(op->tma, op->kind, op->so, op->geom, op->u->slot, op->c, op->d);
+        if (s == FD_OK && op->pair.ready)
+            s = pair_plan_build(op->pair, op->so, op->geom, op->u->slot, op->c, op->d);
         return s != FD_OK ? s : rebuild_fused(op);
     }
     if (n == "m" || n == "eta") {
@@ -685,14 +709,37 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
     if (op->kind == FD_ACOUSTIC_LEAPFROG) {
         cs = prepare_coefficients(op, dt);
         if (cs != FD_OK) return cs;
+        const int sweep = plain ? 1 : acoustic_steps_per_sweep(op);
+        const bool has_rec = op->rec && op->rec->npoint > 0, has_src = op->src && op->src->npoint > 0;
         for (int64_t q = 0; q < nt; q++) {
             int64_t n = reverse ? t0 + nt - 1 - q : t0 + q;
             int cur = (int)((reverse ? n + 1 : n) & 1);
             float *u = op->u->slot[cur];
             float *up = op->u->slot[cur ^ 1];
-            float *rec_row = (op->rec && op->rec->npoint > 0) ? op->rec->trace + n * op->rec->stride : nullptr;
-            const float *src_row =
-                (op->src && op->src->npoint > 0) ? op->src->trace + n * op->src->stride : nullptr;
+            float *rec_row = has_rec ? op->rec->trace + n * op->rec->stride : nullptr;
+            const float *src_row = has_src ? op->src->trace + n * op->src->stride : nullptr;
+            if (sweep == 2 && nt - q >= 2) {
+                // steps n and n2 in one sweep: receivers of n read u^n before
+                // it, those of n2 read u^{n+1} (the buffer of u^{n-1}) after it
+                const int64_t n2 = reverse ? n - 1 : n + 1;
+                if (rec_row) {
+                    FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
+                    op->launches += 1;
+                }
+                FD_CUDA(profile_mark(op, 0), "profile");
+                FD_CUDA(launch_acoustic_pair(op->pair, op->coef, cur, op->status, src_row,
+                                             has_src ? op->src->trace + n2 * op->src->stride : nullptr, st),
+                        "two-step sweep");
+                FD_CUDA(profile_mark(op, 1), "profile");
+                op->launches += 1;
+                if (has_rec) {
+                    FD_CUDA(launch_interpolate(op->rec->dev, up, op->rec->trace + n2 * op->rec->stride, st),
+                            "interpolate");
+                    op->launches += 1;
+                }
+                q++;
+                continue;
+            }
             if (plain) {
                 if (rec_row) {
                     FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
@@ -1042,6 +1089,16 @@ extern "C" fd_status fd_operator_converge(fd_operator *op, int64_t t0, int64_t m
 extern "C" fd_status fd_operator_set_time_block(fd_operator *op, int k)
 {
     if (!op || k < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_set_time_block: bad arguments");
+    if (op->kind == FD_ACOUSTIC_LEAPFROG) {
+        if (k > 2) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_set_time_block: 1 or 2 steps per sweep");
+        if (k == 2 && (!op->pair.ready || !op->tma.ready || (op->flags & FD_FLAG_PLAIN_KERNELS) ||
+                       (op->src && op->src->npoint > 0 && !op->pair.has_src)))
+            return set_error(FD_ERR_UNSUPPORTED,
+                             "fd_operator_set_time_block: no two-step kernel for this operator (SO 4..8, 3D, "
+                             "every column resident, sources fused)");
+        op->want_sweep = k;
+        return FD_OK;
+    }
     if (!op->cluster.ok) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_set_time_block: no cluster path");
     const int old = op->want_k;
     const ClusterPlan keep = op->cluster;
@@ -1058,6 +1115,13 @@ extern "C" fd_status fd_operator_set_time_block(fd_operator *op, int k)
 extern "C" fd_status fd_operator_get_time_block(const fd_operator *op, int *k, int *ctas)
 {
     if (!op || !k || !ctas) return set_error(FD_ERR_INVALID_ARG, "fd_operator_get_time_block: null pointer");
+    if (op->kind == FD_ACOUSTIC_LEAPFROG) {
+        *k = acoustic_steps_per_sweep(op);
+        int rows = 0, stages = 0, c1 = 0;
+        tma_plan_tiling(op->tma, &rows, &stages, &c1);
+        *ctas = *k == 2 ? op->pair.args.k1 * op->pair.args.k2 : (op->tma.ready ? c1 : 0);
+        return FD_OK;
+    }
     *k = op->cluster.ok ? op->cluster.K : 0;
     *ctas = op->cluster.ok ? op->cluster.nctas : 0;
     return FD_OK;

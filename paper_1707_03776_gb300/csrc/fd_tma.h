@@ -107,6 +107,52 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
 cudaError_t launch_acoustic_tma(const TmaPlan &plan, int M, const Geom &g, const Coef &cf,
                                 int cur, int *status, const float *src_row, cudaStream_t st);
 
+// Tensor map of a 3D field of the tiling `a` with a box of box_w x box_h x 1.
+fd_status tma_encode_3d(CUtensorMap *map, float *base, const TileArgs &a, int box_w, int box_h);
+
+// Injected corners of the point set `src` per tile of the tiling `a`, each
+// tile's list sorted by plane: all[off[t] .. off[t+1]) belong to tile t.
+void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vector<SrcEntry> &all,
+                        std::vector<int> &off, int &max_per_tile);
+// Copy the lists to one device allocation (mem_out, freed by the caller).
+fd_status fused_upload(const std::vector<SrcEntry> &all, const std::vector<int> &off, cudaStream_t st,
+                       SparseFused &fused, void *&mem_out);
+
+// ---- two time steps per sweep (k_pair.cu) ---------------------------------
+
+// Plan of the two-step kernel: one CTA per tile column (kz = 1), every column
+// resident at once (cooperative launch), progress flags per column.
+struct PairPlan {
+    bool ready = false;
+    int force_rows = 0;      // > 0: tile height chosen by the caller
+    int M = 0;
+    int stages = 0;          // prefetch depth of the u^n ring
+    TileArgs args{};
+    int threads = 0;
+    size_t smem = 0, smem_max = 0;
+    CUtensorMap u_halo[2];   // slot s of u, haloed box
+    CUtensorMap u_tile[2];   // slot s of u, tile box
+    CUtensorMap c_tile, d_tile;
+    float *slot[2] = {nullptr, nullptr};
+    SparseFused fused;
+    void *fused_mem = nullptr;
+    bool has_src = false;
+    int src_cap = 0;
+    int *progress = nullptr;  // [k1 * k2] planes of u^{n+1} written, per column
+};
+
+// Build the plan (3D acoustic, SO 4..8 only; otherwise ready stays false).
+fd_status pair_plan_build(PairPlan &plan, int space_order, const Geom &g, float *const slot[2], float *c, float *d);
+// Build its fused source table; false in has_src when sources exist but the
+// per-tile lists do not fit (the operator then steps one at a time).
+fd_status pair_sparse_build(PairPlan &plan, const SparseHostView *src, cudaStream_t st);
+void pair_plan_release(PairPlan &plan, cudaStream_t st);
+// Two steps: slot b holds u^n and slot b^1 u^{n-1}; afterwards slot b^1
+// holds u^{n+1} and slot b u^{n+2}.  src_row1 / src_row2 are the source
+// rows of the two steps (null: none).
+cudaError_t launch_acoustic_pair(const PairPlan &plan, const Coef &cf, int b, int *status, const float *src_row1,
+                                 const float *src_row2, cudaStream_t st);
+
 // ---- many shots per launch (k_batch.cu) ----------------------------------
 
 struct ShotDesc;

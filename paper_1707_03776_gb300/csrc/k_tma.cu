@@ -131,6 +131,11 @@ cudaError_t configure_kernel(size_t smem)
 
 }  // namespace
 
+fd_status tma_encode_3d(CUtensorMap *map, float *base, const TileArgs &a, int box_w, int box_h)
+{
+    return encode_3d(map, base, a, box_w, box_h);
+}
+
 fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g, float *const slot[2], float *c,
                          float *d)
 {
@@ -284,22 +289,14 @@ void tma_plan_release(TmaPlan &plan, cudaStream_t st)
     plan.has_src = false;
 }
 
-fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_t st)
+void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vector<SrcEntry> &all,
+                        std::vector<int> &off, int &max_per_tile)
 {
-    if (plan.fused_mem) {
-        cudaStreamSynchronize(st);
-        cudaFree(plan.fused_mem);
-        plan.fused_mem = nullptr;
-    }
-    plan.has_src = false;
-    plan.fused = SparseFused();
-    plan.src_cap = 0;
-    if (!plan.ready) return FD_OK;
-    const TileArgs &a = plan.args;
-    const int M = plan.M;
     const int tiles = a.k1 * a.k2;
-    plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, 0);
-    if (!src || src->npoint <= 0) return FD_OK;
+    all.clear();
+    off.assign(tiles + 1, 0);
+    max_per_tile = 0;
+    if (!src || src->npoint <= 0) return;
     // tile owning grid row i1 and column i2, and that tile's first row/column
     auto owner = [&](int64_t i1, int64_t i2, int &tile, int &row0, int &col0) {
         int strip = (int)(i1 * a.k1 / a.n1);
@@ -332,38 +329,63 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
             per[tile].push_back(e);
         }
     }
-    std::vector<int> off(tiles + 1, 0);
-    std::vector<SrcEntry> all;
-    size_t max_s = 0;
     for (int t = 0; t < tiles; t++) {
         std::stable_sort(per[t].begin(), per[t].end(), [](const SrcEntry &x, const SrcEntry &y) { return x.z < y.z; });
         off[t] = (int)all.size();
         all.insert(all.end(), per[t].begin(), per[t].end());
-        max_s = std::max(max_s, per[t].size());
+        max_per_tile = std::max(max_per_tile, (int)per[t].size());
     }
     off[tiles] = (int)all.size();
-    // the tile's corners are staged in shared memory: lower the prefetch depth
-    // if that is what it takes, else leave injection to its own kernel
-    while (plan.stages > kMinStages &&
-           tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, (int)max_s) > plan.smem_max)
-        plan.stages--;
-    if (tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, (int)max_s) > plan.smem_max) {
-        plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, 0);
-        return FD_OK;
-    }
+}
+
+fd_status fused_upload(const std::vector<SrcEntry> &all, const std::vector<int> &off, cudaStream_t st,
+                       SparseFused &fused, void *&mem_out)
+{
     const size_t b_src = (sizeof(SrcEntry) * all.size() + 15) / 16 * 16;
-    const size_t b_off = sizeof(int) * (tiles + 1);
+    const size_t b_off = sizeof(int) * off.size();
     unsigned char *mem = nullptr;
     if (cudaMalloc((void **)&mem, b_src + b_off + 16) != cudaSuccess) return set_error(FD_ERR_NOMEM, "fused sources");
-    plan.fused_mem = mem;
+    mem_out = mem;
     cudaError_t e = cudaMemcpyAsync(mem, all.data(), sizeof(SrcEntry) * all.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mem + b_src, off.data(), b_off, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(FD_ERR_CUDA, "fused sources: %s", cudaGetErrorString(e));
-    plan.fused.src = (const SrcEntry *)mem;
-    plan.fused.src_off = (const int *)(mem + b_src);
+    fused.src = (const SrcEntry *)mem;
+    fused.src_off = (const int *)(mem + b_src);
+    return FD_OK;
+}
+
+fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_t st)
+{
+    if (plan.fused_mem) {
+        cudaStreamSynchronize(st);
+        cudaFree(plan.fused_mem);
+        plan.fused_mem = nullptr;
+    }
+    plan.has_src = false;
+    plan.fused = SparseFused();
+    plan.src_cap = 0;
+    if (!plan.ready) return FD_OK;
+    const TileArgs &a = plan.args;
+    const int M = plan.M;
+    plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, 0);
+    if (!src || src->npoint <= 0) return FD_OK;
+    std::vector<SrcEntry> all;
+    std::vector<int> off;
+    int max_s = 0;
+    fused_corner_lists(a, src, all, off, max_s);
+    // the tile's corners are staged in shared memory: lower the prefetch depth
+    // if that is what it takes, else leave injection to its own kernel
+    while (plan.stages > kMinStages && tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, max_s) > plan.smem_max)
+        plan.stages--;
+    if (tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, max_s) > plan.smem_max) {
+        plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, 0);
+        return FD_OK;
+    }
+    fd_status s = fused_upload(all, off, st, plan.fused, plan.fused_mem);
+    if (s != FD_OK) return s;
     plan.has_src = true;
-    plan.src_cap = (int)max_s;
+    plan.src_cap = max_s;
     plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, plan.src_cap);
     return FD_OK;
 }
