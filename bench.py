@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    p.add_argument("--rows", default="diffusion,convection,laplace,gradient,batched,learned",
+    p.add_argument("--rows", default="diffusion,convection,laplace,gradient,batched,learned,two_step",
                    help="secondary rows to run (comma-separated)")
     p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
     p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel (default: autotuned)")
@@ -530,6 +530,54 @@ def bench_batched(nshots=64, nt=800, plain_shots=8):
             "launches_per_step": 1, "window_points": pts / nt}
 
 
+def bench_two_step(n=512, so=8, nt=200, reps=3):
+    """Temporal blocking of the grid update: the headline forward workload
+    (512^3 SO8, source and receivers) run with one and with two time steps
+    per sweep on the same operator, bitwise-equal results checked.  The
+    two-step sweep's own HBM traffic is 24 bytes per point per launch (u^n,
+    u^{n-1}, c, d read; u^{n+1}, u^{n+2} written), so its roofline is
+    effective bandwidth = 40 bytes per point per launch / kernel time."""
+    import torch
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    from paper_1707_03776_gb300.modeling import AcousticModel
+    cfg = wl.acoustic_config(n=n, space_order=so, nt=nt)
+    model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], so, cfg["src_coords"], cfg["rec_coords"], nt)
+    model.load(cfg["m"], cfg["eta"], cfg["src_trace"])
+    op = model.op
+    out, res = {}, {}
+    for k in (1, 2):
+        fd.fd_operator_set_time_block(op.handle, k)
+        kk, ctas = fd.fd_operator_get_time_block(op.handle)
+
+        def run():
+            for s in model.u.slots:
+                s.zero_()
+            op.apply(0, nt, cfg["dt"])
+
+        run()
+        op.sync()
+        op.profile(reps * nt)
+        ms = _time_runs(run, reps, warmup=1) / nt
+        op.sync()
+        k_ms, k_n = op.profile_read()
+        res[k] = [t.clone() for t in model.u.slots]
+        out["steps_per_sweep_%d" % k] = {
+            "ms_per_time_step": ms, "GPts_per_s": float(n) ** 3 / (ms * 1e-3) / 1e9, "ctas": ctas,
+            "sweep_ms_avg": (k_ms / k_n) if k_n else None, "time_steps_per_sweep": kk}
+    same = all(torch.equal(a, b) for a, b in zip(res[1], res[2]))
+    two = out["steps_per_sweep_2"]
+    peak, peak_kind = measured_peak_hbm()
+    if two["sweep_ms_avg"]:
+        s_ = two["sweep_ms_avg"] * 1e-3
+        two["hbm_GBs_own_traffic"] = 24.0 * n ** 3 / s_ / 1e9
+        two["effective_GBs"] = 40.0 * n ** 3 / s_ / 1e9
+        two["effective_frac_of_measured_hbm"] = two["effective_GBs"] / peak
+    return {"workload": workload_name(n, so, nt), "bitwise_equal": bool(same),
+            "speedup_two_vs_one": out["steps_per_sweep_1"]["ms_per_time_step"] / two["ms_per_time_step"],
+            "peak_kind": peak_kind, **out}
+
+
 def bench_learned(n=128, nt=2000):
     """The learned-closure row: a coarse 20 m SO4 grid corrected every step
     by the 4-layer BF16 CNN, trained on 128 fine-grid (10 m, SO16) runs of
@@ -735,7 +783,8 @@ def run_ours(args):
     rows = None
     if rank == 0 and not args.no_rows:
         fns = {"diffusion": bench_diffusion, "convection": bench_convection, "laplace": bench_laplace,
-               "gradient": bench_gradient, "batched": bench_batched, "learned": bench_learned}
+               "gradient": bench_gradient, "batched": bench_batched, "learned": bench_learned,
+               "two_step": bench_two_step}
         rows = {name: fns[name]() for name in args.rows.split(",") if name in fns}
 
     if rank == 0:

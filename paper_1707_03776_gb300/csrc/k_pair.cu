@@ -4,13 +4,13 @@
 //
 // One cooperative launch, one CTA per tile column (64 columns of d2, a strip
 // of d1 rows, every d0 plane), every column resident at once.  Each CTA
-// streams its column along d0 with two stages, the second M planes behind the
-// first:
+// streams its column along d0 with two stages, the second L = max(M, 4)
+// planes behind the first:
 //   stage 1  u^{n+1} at plane p from u^n (haloed TMA ring + the d0 register
 //            queue q0), u^{n-1}, c and d: the single-step sweep.  The result
 //            is written in place over u^{n-1} and pushed into a second
 //            register queue q1;
-//   stage 2  u^{n+2} at plane p - M: the d1/d2 neighbours from a haloed TMA
+//   stage 2  u^{n+2} at plane p - L: the d1/d2 neighbours from a haloed TMA
 //            box of u^{n+1} (its halo rows and columns were written by the
 //            neighbouring columns' stage 1 a few planes earlier and are still
 //            in L2), the d0 neighbours from q1, u^n from the oldest entry of
@@ -23,17 +23,26 @@
 //
 // Ordering between columns.  A haloed box reaches only the adjacent columns
 // (strips are at least M rows tall, interior tiles 64 >= 8 columns wide).
-// After stage 1 has stored plane p, thread 0
-// publishes the column's progress (planes of u^{n+1} written) with a release
-// store.  The stage-2 box of plane q is loaded once the (up to 8) neighbouring
-// columns have published q + 1 (acquire, bounded by the global timer).  That
-// one condition also makes the in-place write of u^{n+2} safe: a neighbour
-// that has finished stage 1 at plane q has loaded every u^n plane up to
-// q + M.  Stage 1 reads only the launch's inputs and never waits, and at
-// iteration j a column waits only on columns that have reached iteration
-// j - M + 1, so no wait closes a cycle (M >= 2).  A wait that gives up records
-// FD_ERR_TIMEOUT, and every other column's wait gives up as soon as it sees a
-// non-zero status; each CTA drains the copies it issued before it returns.
+// After stage 1 has stored plane p, thread 0 publishes the column's progress
+// (planes of u^{n+1} written) with a release store.  The stage-2 box of plane
+// q is loaded once the (up to 8) neighbouring columns have published q + 1:
+// warp 0 reads the eight flags with eight lanes at once (acquire, bounded by
+// the global timer) and keeps the smallest value seen, so that most
+// iterations read none.  That one condition also makes the in-place write of
+// u^{n+2} safe: a neighbour that has finished stage 1 at plane q has loaded
+// every u^n plane up to q + M.  Stage 1 reads only the launch's inputs and
+// never waits, and at iteration j a column waits only on columns that have
+// reached iteration j - L + 2 (two planes of slack in lockstep), so no wait
+// closes a cycle.  A wait that gives up records FD_ERR_TIMEOUT, every other
+// column's wait gives up as soon as it sees a non-zero status, and each CTA
+// drains the copies it issued before it returns.
+//
+// Measured on the 512^3 SO8 workload the sweep is slower than two single-step
+// sweeps: a gpu-scope release under full HBM load takes 3-6 us, several
+// plane-iterations, so the columns wait on one another's flags; hiding it
+// would take a lag of 6-8 planes, which the registers (two queues) and the
+// shared memory (two pipelines) of one CTA per SM do not hold.  The operator
+// therefore steps one at a time unless two steps per sweep are asked for.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -101,12 +110,13 @@ __device__ __forceinline__ void fence_proxy_async_global()
 }
 
 // The update at a thread's 4 consecutive d2 points: pc points at the first of
-// them in a haloed plane (row stride kBoxW), q holds the 2M+1 values along d0
-// (centre q[M]); umv, cv, dv are u^{n-1}, c and d there.
-template <int M>
-__device__ __forceinline__ void update4(const float *pc, const float4 (&q)[2 * M + 1], const float umv[4],
+// them in a haloed plane (row stride kBoxW), q[OFF .. OFF+2M] holds the 2M+1
+// values along d0 (centre q[OFF+M]); umv, cv, dv are u^{n-1}, c and d there.
+template <int M, int OFF, int QN>
+__device__ __forceinline__ void update4(const float *pc, const float4 (&q)[QN], const float umv[4],
                                         const float cv[4], const float dv[4], const Coef &cf, float res[4])
 {
+    static_assert(OFF + 2 * M < QN, "queue window");
     constexpr int HV = (M + 3) / 4;  // float4 groups on each side of the thread's 4 points
     constexpr int NR = 4 * (2 * HV + 1);
     float row[NR];
@@ -130,8 +140,8 @@ __device__ __forceinline__ void update4(const float *pc, const float4 (&q)[2 * M
         float lap = cf.centre * u;
 #pragma unroll
         for (int k = 1; k <= M; k++) {
-            const float4 lo = q[M - k];
-            const float4 hi = q[M + k];
+            const float4 lo = q[OFF + M - k];
+            const float4 hi = q[OFF + M + k];
             const float s2 = row[4 * HV + i - k] + row[4 * HV + i + k];
             const float s1 = (&cm[k].x)[i] + (&cp[k].x)[i];
             const float s0 = (&lo.x)[i] + (&hi.x)[i];
@@ -193,12 +203,14 @@ __global__ void __launch_bounds__(kPairThreads, 1)
 {
     constexpr int NU = M + 1 + P;  // u^n planes alive: M behind the newest, the newest, P in flight
     constexpr int NA = P + 1;      // stage-1 (u^{n-1}, c, d) slots
-    constexpr int Q = 2 * M + 1;   // d0 queue length
-    static_assert(M >= 2, "the stage-2 prefetch needs M >= 2 planes of lag");
+    constexpr int L = M > 4 ? M : 4;  // stage 2 trails stage 1 by L planes
+    constexpr int E = L - M;
+    constexpr int Q = 2 * M + 1 + E;  // d0 queues: the stencil window plus E planes of lag
+    static_assert(M >= 2 && L >= M, "two planes of slack need L >= M >= 2");
 
     if (*reinterpret_cast<volatile int *>(status) != 0) return;
-    const PairLayout L = pair_smem_layout(M, P, a.rows_max, src_cap, a.n0);
-    if (L.end > (size_t)dynamic_smem_bytes()) {
+    const PairLayout lay = pair_smem_layout(M, P, a.rows_max, src_cap, a.n0);
+    if (lay.end > (size_t)dynamic_smem_bytes()) {
         if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
         return;
     }
@@ -213,13 +225,13 @@ __global__ void __launch_bounds__(kPairThreads, 1)
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>(smem_raw);
-    float *box = reinterpret_cast<float *>(smem_raw + L.box);
-    float *aux1 = reinterpret_cast<float *>(smem_raw + L.aux1);
-    float *aux2 = reinterpret_cast<float *>(smem_raw + L.aux2);
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw + L.bars);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem_raw + L.abort);
-    SrcEntry *s_src = reinterpret_cast<SrcEntry *>(smem_raw + L.src);
-    int *s_sstart = reinterpret_cast<int *>(smem_raw + L.sstart);
+    float *box = reinterpret_cast<float *>(smem_raw + lay.box);
+    float *aux1 = reinterpret_cast<float *>(smem_raw + lay.aux1);
+    float *aux2 = reinterpret_cast<float *>(smem_raw + lay.aux2);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw + lay.bars);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem_raw + lay.abort);
+    SrcEntry *s_src = reinterpret_cast<SrcEntry *>(smem_raw + lay.src);
+    int *s_sstart = reinterpret_cast<int *>(smem_raw + lay.sstart);
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -245,7 +257,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     const int plane_u = ring_plane_floats(a.box_h);
     const int plane_a = a.rows_max * kTileW;
     const int J1 = a.n0 + 2 * M;  // iterations that load u^n; stage 1 finishes plane j - 2M
-    const int J = a.n0 + 3 * M;   // stage 2 finishes plane j - 3M
+    const int J = a.n0 + 2 * M + L;  // stage 2 finishes plane j - 2M - L
     const uint32_t bytes_u = (uint32_t)(kBoxW * a.box_h * sizeof(float));
     const uint32_t bytes_a1 = (uint32_t)(3 * plane_a * sizeof(float));
     const uint32_t bytes_2 = bytes_u + (uint32_t)(2 * plane_a * sizeof(float));
@@ -267,10 +279,10 @@ __global__ void __launch_bounds__(kPairThreads, 1)
             tma_load_3d(smem_addr(dst + 2 * plane_a), &map_d, col0, row0, ja, bar(NU + sa));
         }
     };
-    // iteration j >= 3M: the haloed u^{n+1} box and the c, d tiles of plane
-    // j - 3M into slot (j - 3M) & 1
+    // iteration j >= 2M + L: the haloed u^{n+1} box and the c, d tiles of
+    // plane j - 2M - L into slot (j - 2M - L) & 1
     auto issue2 = [&](int j) {
-        const int jb = j - 3 * M;
+        const int jb = j - 2 * M - L;
         const int sb = jb & 1;
         const uint32_t b2 = bar(NU + NA + sb);
         mbar_expect_tx(b2, bytes_2);
@@ -282,20 +294,29 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     auto wait_u = [&](int j) { return mbar_wait_bounded(bar(j % NU), (uint32_t)((j / NU) & 1)); };
     auto wait_a = [&](int ja) { return mbar_wait_bounded(bar(NU + ja % NA), (uint32_t)((ja / NA) & 1)); };
     auto wait_b = [&](int jb) { return mbar_wait_bounded(bar(NU + NA + (jb & 1)), (uint32_t)((jb >> 1) & 1)); };
-    // thread 0: until every neighbouring column has written u^{n+1} planes
-    // [0, need); gives up after the wait limit, or at once when another CTA
-    // has recorded an error
+    // warp 0: until every neighbouring column has written u^{n+1} planes
+    // [0, need).  Lane l < 8 reads the flag of neighbour l; seen keeps the
+    // smallest value read, so a wait already covered reads nothing.  Gives up
+    // after the wait limit, or at once when a CTA has recorded an error.
+    const int *nb_flag = nullptr;
+    if (tid < 8) {
+        const int o = tid < 4 ? tid : tid + 1;  // 3 x 3 neighbourhood without its centre
+        const int s = strip + o / 3 - 1, t = t2 + o % 3 - 1;
+        if (s >= 0 && s < a.k1 && t >= 0 && t < a.k2) nb_flag = progress + s * a.k2 + t;
+    }
+    int seen = -1;
     auto neighbours_ready = [&](int need) {
+        if (seen >= need) return true;
         const unsigned long long t0 = global_ns();
-        for (int ds = -1; ds <= 1; ds++)
-            for (int dc = -1; dc <= 1; dc++) {
-                const int s = strip + ds, t = t2 + dc;
-                if ((ds == 0 && dc == 0) || s < 0 || s >= a.k1 || t < 0 || t >= a.k2) continue;
-                const int *f = progress + s * a.k2 + t;
-                while (ld_acquire(f) < need)
-                    if (*reinterpret_cast<volatile int *>(status) != 0 || global_ns() - t0 > kWaitLimitNs)
-                        return false;
-            }
+        for (;;) {
+            const int v = nb_flag ? ld_acquire(nb_flag) : 0x7fffffff;
+            seen = __reduce_min_sync(0xffffffffu, v);
+            if (seen >= need) break;
+            const bool give_up =
+                *reinterpret_cast<volatile int *>(status) != 0 || global_ns() - t0 > kWaitLimitNs;
+            if (__any_sync(0xffffffffu, give_up)) return false;
+        }
+        __syncwarp();
         return true;
     };
 
@@ -322,8 +343,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         __syncthreads();
     }
 
-    // q0[k]: u^n at plane j - 3M + k (the thread's 4 points); q1[k]: u^{n+1}
-    // at plane j - 4M + k, after the pushes of iteration j
+    // after the pushes of iteration j: q0[k] holds u^n at plane
+    // j - 3M - E + k (the thread's 4 points), q1[k] u^{n+1} at plane
+    // j - 3M - L + k
     float4 q0[Q], q1[Q];
 #pragma unroll
     for (int k = 0; k < Q; k++) {
@@ -334,19 +356,21 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     int j = 0;
     bool ok = true, stop = false;
     for (; j < J; j++) {
-        if (tid == 0) {
-            if (j + P < J1) {
+        if (tid < 32) {
+            if (tid == 0 && j + P < J1) {
                 issue1(j + P);
                 issued1 = j + P;
             }
             const int jn = j + 1;
-            if (jn >= 3 * M && jn < J) {
-                // this column has written planes [0, j - 2M) >= jn - 3M + 1
-                if (neighbours_ready(jn - 3 * M + 1)) {
-                    fence_proxy_async_global();
-                    issue2(jn);
-                    issued2 = jn;
-                } else {
+            if (jn >= 2 * M + L && jn < J) {
+                // this column has written planes [0, j - 2M), >= jn - 2M - L + 2
+                if (neighbours_ready(jn - 2 * M - L + 1)) {
+                    if (tid == 0) {
+                        fence_proxy_async_global();
+                        issue2(jn);
+                        issued2 = jn;
+                    }
+                } else if (tid == 0) {
                     *abort_flag = 1;
                 }
             }
@@ -373,7 +397,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                 const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
                 const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
                 float res[4];
-                update4<M>(pc, q0, umv, cv, dv, cf, res);
+                update4<M, E, Q>(pc, q0, umv, cv, dv, cf, res);
                 if (nsrc > 0) inject4(res, cv, s_src, s_sstart, ja, r, qc, src_row1);
                 store4(out1, a, ja, row0 + r, col0 + 4 * qc, res);
                 v1 = make_float4(res[0], res[1], res[2], res[3]);
@@ -383,9 +407,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         for (int k = 0; k < Q - 1; k++) q1[k] = q1[k + 1];
         q1[Q - 1] = v1;
 
-        // stage 2: u^{n+2} at plane j - 3M
-        if (j >= 3 * M) {
-            const int jb = j - 3 * M;
+        // stage 2: u^{n+2} at plane j - 2M - L
+        if (j >= 2 * M + L) {
+            const int jb = j - 2 * M - L;
             ok = wait_b(jb) && ok;
             if (ok && active) {
                 const float *pc = box + (jb & 1) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc;
@@ -396,7 +420,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                 const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
                 const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
                 float res[4];
-                update4<M>(pc, q1, umv, cv, dv, cf, res);
+                update4<M, 0, Q>(pc, q1, umv, cv, dv, cf, res);
                 if (nsrc > 0) inject4(res, cv, s_src, s_sstart, jb, r, qc, src_row2);
                 store4(out2, a, jb, row0 + r, col0 + 4 * qc, res);
             }
@@ -410,10 +434,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
             stop = true;
             break;
         }
-        if (tid == 0 && wrote1) {
-            __threadfence();
-            st_release(progress + tile, j - 2 * M + 1);
-        }
+        // the release orders every thread's stores of this plane (they
+        // happen before it through the barrier) before the flag
+        if (tid == 0 && wrote1) st_release(progress + tile, j - 2 * M + 1);
     }
 
     if (stop) {
@@ -429,8 +452,8 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                     mbar_wait_until(bar(NU + ia % NA), (uint32_t)((ia / NA) & 1), deadline);
                 }
             }
-            for (int i = j > 3 * M ? j : 3 * M; i <= issued2; i++) {
-                const int ib = i - 3 * M;
+            for (int i = j > 2 * M + L ? j : 2 * M + L; i <= issued2; i++) {
+                const int ib = i - 2 * M - L;
                 mbar_wait_until(bar(NU + NA + (ib & 1)), (uint32_t)((ib >> 1) & 1), deadline);
             }
         }
@@ -454,6 +477,10 @@ int pair_occupancy(int threads, size_t smem)
         return 0;
     return occ;
 }
+
+// threads of a CTA: 16 per row, whole warps (warp 0 polls with full-warp
+// reductions; the extra lanes own no points)
+int pair_threads(int rows_max) { return (16 * rows_max + 31) / 32 * 32; }
 
 int occupancy_of(int M, int threads, size_t smem)
 {
@@ -517,7 +544,7 @@ fd_status pair_plan_build(PairPlan &plan, int space_order, const Geom &g, float 
         const size_t smem = pair_smem_layout(M, kPairStages, rows_max, 0, a.n0).end;
         if (smem + reserve > (size_t)smem_max) continue;
         if (cols > 8LL * sms) break;
-        const int occ = occupancy_of(M, 16 * rows_max, smem);
+        const int occ = occupancy_of(M, pair_threads(rows_max), smem);
         if (occ < 1 || cols > (long long)sms * occ) continue;
         const double cost = (double)((cols + sms - 1) / sms) * (rows_max + 0.5 * M);
         if (best_k1 < 0 || cost < best_cost - 1e-9) {
@@ -536,7 +563,7 @@ fd_status pair_plan_build(PairPlan &plan, int space_order, const Geom &g, float 
     plan.M = M;
     plan.stages = kPairStages;
     plan.args = a;
-    plan.threads = 16 * a.rows_max;
+    plan.threads = pair_threads(a.rows_max);
     plan.smem = pair_smem_layout(M, kPairStages, a.rows_max, 0, a.n0).end;
     plan.smem_max = (size_t)smem_max;
     plan.slot[0] = slot[0];
