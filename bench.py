@@ -779,6 +779,17 @@ def run_ours(args):
         cpu = {"value": v, "unit": "GPts/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": "%d of %d time steps of the same %d^3 SO%d forward run, FP32 loop nest, %.1f s" % (
                    args.cpu_steps, args.nt, args.n, args.so, el)}
+        # the same loop nest on one core, and the FP64 loop nest on all cores
+        # (one step each)
+        v64, el64 = oracle_sample(cfg, args.so, 1, precision="f64")
+        oracle.set_num_threads(1)
+        try:
+            v1, el1 = oracle_sample(cfg, args.so, 1)
+        finally:
+            oracle.set_num_threads(None)
+        cpu["one_core_f32"] = {"value": v1, "unit": "GPts/s", "cores": 1, "s": el1, "steps": 1}
+        cpu["all_cores_f64"] = {"value": v64, "unit": "GPts/s", "cores": oracle.num_threads(), "s": el64,
+                                "steps": 1}
 
     rows = None
     if rank == 0 and not args.no_rows:

@@ -267,8 +267,14 @@ def step_points(shape, spacing, space_order, m, eta, dt, u_cur32, u_prev32, flat
     return out
 
 
+_THREADS = None
+
+
 def num_threads():
-    """Threads the OpenMP loops of the oracle use (OMP_NUM_THREADS or cores)."""
+    """Threads the OpenMP loops of the oracle use (set_num_threads, else
+    OMP_NUM_THREADS, else the cores)."""
+    if _THREADS is not None:
+        return _THREADS
     env = os.environ.get("OMP_NUM_THREADS")
     if env:
         try:
@@ -276,6 +282,22 @@ def num_threads():
         except ValueError:
             pass
     return os.cpu_count() or 1
+
+
+def set_num_threads(n):
+    """Threads for the oracle's later OpenMP loops (the OpenMP runtime's own
+    omp_set_num_threads, reached through the loaded library); None restores
+    the default."""
+    global _THREADS
+    fn = _lib().omp_set_num_threads
+    fn.argtypes = [ctypes.c_int]
+    fn.restype = None
+    if n is None:
+        _THREADS = None
+        fn(ctypes.c_int(num_threads()))
+    else:
+        _THREADS = int(n)
+        fn(ctypes.c_int(_THREADS))
 
 
 def acoustic_gradient(shape, spacing, origin, space_order, m64, eta64, dt, nt, src_coords, src_trace,
