@@ -7,6 +7,7 @@ exits 0.  Sizes default to inputs larger than L2 (129 MB) with a few GB on
 the device at most.
 
   acoustic   the tiled grid update (512^3 SO8 by default)
+  pair       the same run with two time steps per sweep (the two-step kernel)
   batch      the batched-shots persistent kernel (8 windows of the 512^3 model)
   gradient   forward, checkpoint recomputation, adjoint and imaging of one
              shot (256^3 SO8, 100 steps, checkpoints every 10 steps)
@@ -37,6 +38,20 @@ def case_acoustic(args):
     if args.tiling:
         rows, stages = (int(x) for x in args.tiling.split(","))
         fd.fd_operator_set_tiling(model.op.handle, rows, stages)
+    model.run(cfg["dt"])
+    model.op.sync()
+    _sync()
+
+
+def case_pair(args):
+    import torch
+    from . import fd, workloads as wl
+    from .modeling import AcousticModel
+    cfg = wl.acoustic_config(n=args.n, space_order=args.so, nt=args.nt)
+    model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], args.so, cfg["src_coords"],
+                          cfg["rec_coords"], args.nt)
+    model.load(torch.from_numpy(cfg["m"]), torch.from_numpy(cfg["eta"]), torch.from_numpy(cfg["src_trace"]))
+    fd.fd_operator_set_time_block(model.op.handle, 2)
     model.run(cfg["dt"])
     model.op.sync()
     _sync()
@@ -145,7 +160,7 @@ def case_wgrad(args):
     _sync()
 
 
-CASES = {"acoustic": case_acoustic, "batch": case_batch, "gradient": case_gradient, "diffusion": case_diffusion,
+CASES = {"acoustic": case_acoustic, "pair": case_pair, "batch": case_batch, "gradient": case_gradient, "diffusion": case_diffusion,
          "conv": case_conv, "conv_tc": case_conv_tc, "wgrad": case_wgrad}
 
 
@@ -161,7 +176,7 @@ def main(argv=None):
     p.add_argument("--stages", type=int, default=2)
     p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel")
     args = p.parse_args(argv)
-    defaults = {"acoustic": (512, 10), "batch": (None, 10), "gradient": (256, 100), "diffusion": (256, 500),
+    defaults = {"acoustic": (512, 10), "pair": (512, 10), "batch": (None, 10), "gradient": (256, 100), "diffusion": (256, 500),
                 "conv": (160, None), "conv_tc": (160, None), "wgrad": (96, None)}
     n, nt = defaults[args.case]
     args.n = args.n or n
