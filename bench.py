@@ -490,7 +490,7 @@ def bench_batched(nshots=64, nt=800, plain_shots=8):
     del plain_ops
     # autotune the batch's tile height and depth on a short run
     best = None
-    for rows in (10, 12, 14, 16, 20):
+    for rows in (10, 12, 14, 16, 20, 24, 28, 32):
         for stages in (2, 3, 4):
             try:
                 b = fd.Batch([s["op"] for s in shots], rows=rows, stages=stages)

@@ -133,6 +133,54 @@ __device__ __forceinline__ double block_sum2(float hi, float lo, float *scratch)
     return t;
 }
 
+// Block-wide compensated sum left in every thread: each warp reduces the
+// warps' pairs itself after one barrier (the butterfly of exact TwoSum steps
+// gives every lane the same bits).  scratch holds 64 floats.
+__device__ __forceinline__ void block_sum2_all(float &hi, float &lo, float *scratch)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        sum2_add(hi, lo, oh, ol);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        scratch[2 * w] = hi;
+        scratch[2 * w + 1] = lo;
+    }
+    __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
+    hi = l < nw ? scratch[2 * l] : 0.0f;
+    lo = l < nw ? scratch[2 * l + 1] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        sum2_add(hi, lo, oh, ol);
+    }
+}
+
+// |a - b| < t * b for double-float a = (ah, al), b = (bh, bl) > 0 and
+// t = (th, tl): the difference and the product carried to ~48 bits (TwoSum,
+// and TwoProd with fmaf), then compared as double-float numbers.
+__device__ __forceinline__ bool df_rel_below(float ah, float al, float bh, float bl, float th, float tl)
+{
+    float dh = ah - bh;
+    const float bp = dh - ah;
+    float dl = ((ah - (dh - bp)) + (-bh - bp)) + (al - bl);
+    const float s = dh + dl;  // renormalise the difference
+    dl = dl - (s - dh);
+    dh = s;
+    if (dh < 0.0f) {
+        dh = -dh;
+        dl = -dl;
+    }
+    const float ph = th * bh;
+    const float pl = fmaf(th, bh, -ph) + (th * bl + tl * bh);
+    const float q = ph + pl;
+    const float ql = pl - (q - ph);
+    return dh < q || (dh == q && dl < ql);
+}
+
 template <int RULE, int M>
 __global__ void __launch_bounds__(kCThreads, 1)
     cluster_stencil_kernel(const ClusterArgs a, const RuleArgs ra, const float *__restrict__ u0, float *slot0,
@@ -149,8 +197,8 @@ __global__ void __launch_bounds__(kCThreads, 1)
     buf[1] = buf[0] + HR * W;
     float *inbox = buf[1] + HR * W;                        // [2 parities][2 sides][H][cols]
     double *part = reinterpret_cast<double *>(inbox + 4 * H * a.cols);  // [2] partial sums
-    float *scratch = reinterpret_cast<float *>(part + 2);  // [32 warps][hi, lo]
-    volatile int *flag = reinterpret_cast<volatile int *>(scratch + 64);
+    float *scratch = reinterpret_cast<float *>(part + 2);  // [2 parities][32 warps][hi, lo]
+    volatile int *flag = reinterpret_cast<volatile int *>(scratch + 128);
 
     const int r0 = (int)((long long)rank * a.rows / a.nctas);
     const int r1 = (int)((long long)(rank + 1) * a.rows / a.nctas);
@@ -184,21 +232,64 @@ __global__ void __launch_bounds__(kCThreads, 1)
         buf[1][q] = 0.0f;
         if (converge && gr >= r0 && gr < r1 && c >= 0 && c < a.cols) sum2_add(sh, sl, fabsf(v), 0.0f);
     }
-    // the convergence state lives in thread 0 of every CTA (all take the same
-    // decision from the same partial sums) and reaches the others by `flag`
-    double s_old = 0.0;
-    if (converge) {
-        const double t = block_sum2(sh, sl, scratch);
-        if (tid == 0) part[1] = t;
-    }
-    barrier();
-    if (converge && tid == 0)
-        for (int k = 0; k < a.nctas; k++) s_old += part_of(k, 1);
-
     int cur = 0, par = 0;
     long long done = 0;
     double r_last = INFINITY;
     bool stop = false;
+    if (RULE == kRuleJacobi && converge && alone) {
+        // One CTA to convergence: one barrier per sweep.  Every thread holds
+        // S^n as a double-float pair and takes the same decision from the
+        // same bits, so no flag and no FP64 arithmetic are needed in the loop.
+        float oh = sh, ol = sl;
+        block_sum2_all(oh, ol, scratch);
+        par = 1;  // the first sweep's partials go to the other scratch half
+        const float th = (float)tol, tl = (float)(tol - (double)th);
+        float dh = 0.0f, dl = 0.0f, ph = 0.0f, pl = 0.0f;
+        while (done < nt) {
+            sh = sl = 0.0f;
+            const float *src = buf[cur];
+            float *dst = buf[cur ^ 1];
+            if (lane_on)
+                for (int lr = tr; lr < nr; lr += a.tr) {
+                    const int base = (lr + H) * W + a.hc;
+                    for (int c = tc; c < a.cols; c += a.tc) {
+                        const float v = apply_rule<RULE, M>(src, base + c, W, lr, c, a, ra);
+                        dst[base + c] = v;
+                        sum2_add(sh, sl, fabsf(v), 0.0f);
+                    }
+                }
+            cur ^= 1;
+            done++;
+            // the barrier inside also orders this sweep's writes before the
+            // next sweep's reads; the scratch halves alternate by parity
+            block_sum2_all(sh, sl, scratch + 64 * par);
+            par ^= 1;
+            const bool hit = oh > 0.0f && df_rel_below(sh, sl, oh, ol, th, tl);
+            ph = oh;
+            pl = ol;
+            dh = sh;
+            dl = sl;
+            oh = sh;
+            ol = sl;
+            if (hit) break;
+        }
+        if (done > 0 && ph > 0.0f) {
+            const double sn = (double)dh + (double)dl, so = (double)ph + (double)pl;
+            r_last = fabs(sn - so) / so;
+        }
+        stop = true;
+    }
+    // the convergence state lives in thread 0 of every CTA (all take the same
+    // decision from the same partial sums) and reaches the others by `flag`
+    double s_old = 0.0;
+    if (converge && !stop) {
+        const double t = block_sum2(sh, sl, scratch);
+        if (tid == 0) part[1] = t;
+    }
+    if (!stop) barrier();
+    if (converge && !stop && tid == 0)
+        for (int k = 0; k < a.nctas; k++) s_old += part_of(k, 1);
+
     while (done < nt && !stop) {
         // the L1 criterion is taken after every sweep: blocks of one step
         const int Kb = converge ? 1 : (int)((nt - done) < (long long)a.K ? (nt - done) : (long long)a.K);
@@ -290,9 +381,9 @@ __global__ void __launch_bounds__(kCThreads, 1)
 
 size_t cluster_smem_bytes(int strip, int halo, int width, int cols)
 {
-    // two buffers, the inboxes, 2 partial sums, 32 warps' (hi, lo), a flag
+    // two buffers, the inboxes, 2 partial sums, 2 x 32 warps' (hi, lo), a flag
     return sizeof(float) * (2 * (size_t)(strip + 2 * halo) * width + 4 * (size_t)halo * cols) +
-           sizeof(double) * 2 + sizeof(float) * 64 + 16;
+           sizeof(double) * 2 + sizeof(float) * 128 + 16;
 }
 
 template <int RULE, int M>
