@@ -294,9 +294,11 @@ fd_status fd_operator_set_time_block(fd_operator *op, int k);
  * kernels). */
 fd_status fd_operator_get_time_block(const fd_operator *op, int *k, int *ctas);
 
-/* Test hook of the failure path: with plane >= 0, the tiled kernel's first
- * tile never receives the copy of u^n plane `plane` (its barrier is armed,
- * the copy not issued), so that CTA's bounded wait gives up after ~2 s,
+/* Test hook of the failure path: with plane >= 0, the first tile of the tiled
+ * kernel (and of the two-step kernel) never receives the copy of u^n plane
+ * `plane` (its barrier is armed, the copy not issued), so that CTA's bounded
+ * wait gives up after ~2 s (in the two-step kernel the other columns then
+ * stop waiting on its progress as soon as they see the status),
  * records FD_ERR_TIMEOUT, drains its copies and returns; later launches do
  * nothing until fd_operator_sync reports and clears the status.  -1 turns it
  * off.  Errors: FD_ERR_UNSUPPORTED when the operator has no tiled kernel. */

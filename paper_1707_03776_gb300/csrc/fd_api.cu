@@ -943,6 +943,7 @@ extern "C" fd_status fd_operator_debug_stall(fd_operator *op, int plane)
     if (!op->tma.ready) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_debug_stall: no tiled kernel");
     op->tma.stall_plane = plane;
     op->tma.args.stall_plane = plane;
+    op->pair.args.stall_plane = plane;
     return FD_OK;
 }
 

@@ -268,7 +268,10 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     auto issue1 = [&](int j) {
         const int su = j % NU;
         mbar_expect_tx(bar(su), bytes_u);
-        tma_load_3d(smem_addr(ring + su * plane_u), &map_u0, col0 - kSideHalo, row0 - M, j - M, bar(su));
+        // the stall hook arms the barrier but never issues the copy, so the
+        // wait for this plane runs out (the failure path under test)
+        if (a.stall_plane < 0 || tile != 0 || j - M != a.stall_plane)
+            tma_load_3d(smem_addr(ring + su * plane_u), &map_u0, col0 - kSideHalo, row0 - M, j - M, bar(su));
         if (j >= 2 * M) {
             const int ja = j - 2 * M;
             const int sa = ja % NA;

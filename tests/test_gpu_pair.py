@@ -136,3 +136,30 @@ def test_two_steps_full_size_bitwise():
     assert np.abs(out[0][0]).max() > 0 and np.abs(out[0][2]).max() > 0
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
+
+
+def test_two_steps_bounded_wait_gives_up_and_reports():
+    """The failure path of the cooperative launch: tile 0 never receives one
+    u^n plane, its bounded wait gives up and records FD_ERR_TIMEOUT, the other
+    columns stop waiting on its progress as soon as they see the status, every
+    CTA drains the copies it issued, and the next run is exact again."""
+    import time
+    args, dt = _case((24, 40, 130), 8, 6, 5)
+    run = AcousticRun(*args)
+    fd.fd_operator_set_time_block(run.op.handle, 2)
+    assert fd.fd_operator_get_time_block(run.op.handle)[1] > 1
+    fd.fd_operator_debug_stall(run.op.handle, 7)
+    t0 = time.perf_counter()
+    run.op.apply(0, 4, dt)
+    with pytest.raises(fd.FDError) as e:
+        run.op.sync()
+    assert e.value.status == fd.FD_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    fd.fd_operator_debug_stall(run.op.handle, -1)
+    for s in run.u.slots:
+        s.zero_()
+    run.run(0, 6, dt)
+    ref = _run(args, dt, 2)
+    for a, b in zip(_slots(run), _slots(ref)):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(run.rec_trace(), ref.rec_trace())
