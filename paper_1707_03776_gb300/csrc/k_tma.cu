@@ -110,10 +110,12 @@ fd_status encode_3d(CUtensorMap *map, float *base, const TileArgs &a, int box_w,
     return FD_OK;
 }
 
-// prefetch depth: planes in flight per CTA; the kernel is latency-bound
-// below ~4 (one CTA per SM keeps P x (haloed u^n + u^{n-1}, c, d tiles) in
-// flight), so the planner takes the deepest that fits
+// prefetch depth: planes in flight per CTA.  The planner takes the deepest
+// up to kPlanStages that keeps the CTAs per SM of the minimum depth (on 512^3
+// a fourth plane was never faster than a third, and costs shared memory);
+// fd_operator_set_tiling may ask for up to kMaxStages.
 constexpr int kMinStages = 2;
+constexpr int kPlanStages = 3;
 constexpr int kMaxStages = 4;
 constexpr size_t kSparseReserve = 16 * 1024;  // shared memory kept for fused point lists
 
@@ -166,9 +168,12 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
         return std::max(occ, 0);
     };
     // Choose the strip count k1 (tile height rows = ceil(n1/k1)): minimise the
-    // work of the busiest SM, ceil(ctas / SMs) tiles of rows + M/2 row-planes
-    // (halo rows cost TMA traffic, served mostly from L2), with every tile of
-    // one wave resident at once; ties go to taller tiles.
+    // work of the busiest SM, ceil(ctas / SMs) tiles of rows + 4M row-planes
+    // (the 2M halo rows of a box cost about twice an interior row: TMA
+    // traffic served from L2 and the barrier wait for it), with every tile of
+    // one wave resident at once.  Two or more CTAs sharing an SM hide each
+    // other's per-plane barrier waits, worth a factor 1.5 (measured on 512^3
+    // SO4/8/16 sweeps of tile height and depth).  Ties go to taller tiles.
     // The d0 chunk count kz multiplies the CTAs only for grids whose columns
     // alone leave SMs idle (up to the resident slots of all SMs); a chunk
     // costs its planes plus the 2M it loads before its first output plane
@@ -186,7 +191,10 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
         const long long per_sm = (ctas + sms - 1) / sms;
         const long long waves = (per_sm + occ - 1) / occ;
         const double planes = (double)((a.n0 + kz - 1) / kz) + 0.35 * 2 * M;
-        return (double)waves * occ * (rows_max + 0.5 * M) * planes * (per_sm > occ ? 1.0 : (double)per_sm / occ);
+        const long long resident = per_sm < occ ? per_sm : occ;
+        const double overlap = resident >= 2 ? 1.5 : 1.0;
+        return (double)waves * occ * (rows_max + 4.0 * M) * planes * (per_sm > occ ? 1.0 : (double)per_sm / occ) /
+               overlap;
     };
     int best_k1 = -1, best_kz = 1;
     double best_cost = 0;
@@ -226,11 +234,14 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     a.rows_max = (a.n1 + a.k1 - 1) / a.k1;
     a.box_h = a.rows_max + 2 * M;
 
-    // deepest prefetch that keeps the occupancy of the minimum depth
+    // deepest prefetch that still holds, per SM, the CTAs of one wave at the
+    // minimum depth (the tiling may place fewer per SM than fit)
+    const long long ctas = (long long)a.k1 * a.k2 * a.kz;
     const int occ2 = occupancy(a.rows_max, kMinStages);
+    const int need = (int)std::min<long long>(occ2, (ctas + sms - 1) / sms);
     int P = kMinStages;
-    for (int p = kMaxStages; p > kMinStages; p--)
-        if (occupancy(a.rows_max, p) >= occ2 &&
+    for (int p = kPlanStages; p > kMinStages; p--)
+        if (occupancy(a.rows_max, p) >= need &&
             tma_smem_bytes(M, p, a.rows_max, a.n0, 0) + kSparseReserve <= (size_t)smem_max) {
             P = p;
             break;
