@@ -164,7 +164,8 @@ struct BatchPlan {
     Coef cf{};
     ShotDesc *d_shots = nullptr;
     BatchItem *d_items = nullptr;
-    int *d_off = nullptr;
+    int *d_next = nullptr;   // next item to take (reset before every launch)
+    int nitems = 0;
 };
 
 // Build the device tables of a batch from the shots' tiled plans (all of the

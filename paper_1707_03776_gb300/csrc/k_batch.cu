@@ -23,8 +23,9 @@
 
 namespace fdgb {
 
-// Per-shot state the batch kernel reads (64-byte aligned for the tensor maps).
-struct alignas(64) ShotDesc {
+// Per-shot state the batch kernel reads (128-byte aligned, as its tensor maps
+// are).
+struct alignas(128) ShotDesc {
     CUtensorMap u_halo[2];
     CUtensorMap u_tile[2];
     CUtensorMap c_tile;
@@ -54,9 +55,9 @@ using namespace tile_dev;
 
 template <int M, int P>
 __global__ void __launch_bounds__(16 * kMaxRows, 1)
-    acoustic_batch_kernel(const ShotDesc *__restrict__ shots, const BatchItem *__restrict__ items,
-                          const int *__restrict__ item_off, const Coef cf, const int rows_max, const int src_cap,
-                          const long long n, const int cur, int *status)
+    acoustic_batch_kernel(const ShotDesc *__restrict__ shots, const BatchItem *__restrict__ items, const int nitems,
+                          int *next_item, const Coef cf, const int rows_max, const int src_cap, const long long n,
+                          const int cur, int *status)
 {
     if (*reinterpret_cast<volatile int *>(status) != 0) return;
     // everything but the per-plane starts (checked per shot below)
@@ -65,8 +66,14 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
     const SweepSmem sm = carve_smem<M, P>(smem_raw, rows_max, src_cap);
     init_barriers<M, P>(sm);
     unsigned it_u = 0, it_a = 0;
-    const int k_end = item_off[blockIdx.x + 1];
-    for (int k = item_off[blockIdx.x]; k < k_end; k++) {
+    // items are sorted by decreasing cost; each CTA takes the next one as
+    // soon as it is free (longest processing time first, balanced at run time)
+    for (;;) {
+        if (threadIdx.x == 0) *sm.item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int k = *sm.item;
+        __syncthreads();
+        if (k >= nitems) break;
         const BatchItem it = items[k];
         const ShotDesc *sd = shots + it.shot;
         if (it.kind == 0) {
@@ -165,30 +172,14 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
             cost.push_back((hi - lo) / 128.0);
         }
     }
-    // longest processing time first onto the least loaded CTA
+    // one list in decreasing cost (receiver chunks, the cheapest, last); the
+    // kernel's CTAs take items from it in order as they become free
     std::vector<int> order(items.size());
     for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    typedef std::pair<double, int> Load;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int c = 0; c < nctas; c++) heap.push(Load(0.0, c));
-    std::vector<std::vector<int>> per(nctas);
-    for (int i : order) {
-        Load l = heap.top();
-        heap.pop();
-        per[l.second].push_back(i);
-        l.first += cost[i];
-        heap.push(l);
-    }
     std::vector<BatchItem> flat;
-    std::vector<int> off(nctas + 1, 0);
-    for (int c = 0; c < nctas; c++) {
-        // columns first, receivers last (their gathers do not block the sweeps)
-        std::stable_sort(per[c].begin(), per[c].end(), [&](int x, int y) { return items[x].kind < items[y].kind; });
-        off[c] = (int)flat.size();
-        for (int i : per[c]) flat.push_back(items[i]);
-    }
-    off[nctas] = (int)flat.size();
+    flat.reserve(order.size());
+    for (int i : order) flat.push_back(items[i]);
 
     std::vector<ShotDesc> shots(nshots);
     for (int s = 0; s < nshots; s++) {
@@ -219,14 +210,11 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
     const size_t b_shots = sizeof(ShotDesc) * nshots;
     const size_t b_items = (sizeof(BatchItem) * std::max<size_t>(flat.size(), 1) + 255) / 256 * 256;
     unsigned char *mem = nullptr;
-    if (cudaMalloc((void **)&mem, b_shots + b_items + sizeof(int) * (nctas + 1)) != cudaSuccess)
+    if (cudaMalloc((void **)&mem, b_shots + b_items + sizeof(int)) != cudaSuccess)
         return set_error(FD_ERR_NOMEM, "batch: device tables");
     cudaError_t e = cudaMemcpyAsync(mem, shots.data(), b_shots, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !flat.empty())
         e = cudaMemcpyAsync(mem + b_shots, flat.data(), sizeof(BatchItem) * flat.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(mem + b_shots + b_items, off.data(), sizeof(int) * (nctas + 1), cudaMemcpyHostToDevice,
-                            st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(mem);
@@ -253,7 +241,8 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
     bp.cf = cf;
     bp.d_shots = (ShotDesc *)mem;
     bp.d_items = (BatchItem *)(mem + b_shots);
-    bp.d_off = (int *)(mem + b_shots + b_items);
+    bp.d_next = (int *)(mem + b_shots + b_items);
+    bp.nitems = (int)flat.size();
     return FD_OK;
 }
 
@@ -262,17 +251,20 @@ void batch_plan_release(BatchPlan &bp)
     if (bp.d_shots) cudaFree(bp.d_shots);
     bp.d_shots = nullptr;
     bp.d_items = nullptr;
-    bp.d_off = nullptr;
+    bp.d_next = nullptr;
+    bp.nitems = 0;
 }
 
 cudaError_t launch_batch(const BatchPlan &bp, long long n, int cur, int *status, cudaStream_t st)
 {
+    cudaError_t e0 = cudaMemsetAsync(bp.d_next, 0, sizeof(int), st);
+    if (e0 != cudaSuccess) return e0;
     const int key = bp.M * 8 + bp.P;
     switch (key) {
 #define CASE(MM, PP)                                                                                          \
     case MM * 8 + PP:                                                                                         \
         acoustic_batch_kernel<MM, PP><<<bp.nctas, bp.threads, bp.smem, st>>>(                                 \
-            bp.d_shots, bp.d_items, bp.d_off, bp.cf, bp.rows_max, bp.src_cap, n, cur, status);               \
+            bp.d_shots, bp.d_items, bp.nitems, bp.d_next, bp.cf, bp.rows_max, bp.src_cap, n, cur, status);   \
         break;
 #define CASES(MM) CASE(MM, 2) CASE(MM, 3) CASE(MM, 4)
         CASES(1) CASES(2) CASES(3) CASES(4) CASES(5) CASES(6) CASES(7) CASES(8)

@@ -102,7 +102,8 @@ __host__ __device__ constexpr int round_up32(int x) { return (x + 31) / 32 * 32;
 __host__ __device__ inline int ring_plane_floats(int box_h) { return round_up32(box_h * kBoxW); }
 
 // Byte offsets of the areas of a tiled CTA's dynamic shared memory: the u^n
-// ring, the aux ring, the mbarriers, the abort flag (16 bytes), then src_cap
+// ring, the aux ring, the mbarriers, the abort flag and the batch kernel's
+// item slot (16 bytes), then src_cap
 // injected corners of the tile and their n0 + 1 per-plane starts.  Both the
 // size a launch requests and the carve in the kernel come from here.
 struct SmemLayout {
@@ -140,6 +141,7 @@ struct SweepSmem {
     float *aux;                  // NA slots of 3 boxes of plane_a floats
     unsigned long long *bars;    // NU + NA mbarriers
     volatile int *abort;
+    int *item;                   // batch kernel: the work item being taken (next to abort)
     SrcEntry *src;               // the column's injected corners
     int *sstart;                 // per-plane starts into src
     int plane_u, plane_a;
@@ -176,6 +178,7 @@ __device__ inline SweepSmem carve_smem(unsigned char *raw, int rows_max, int src
     sm.aux = reinterpret_cast<float *>(raw + l.aux);
     sm.bars = reinterpret_cast<unsigned long long *>(raw + l.bars);
     sm.abort = reinterpret_cast<volatile int *>(raw + l.abort);
+    sm.item = reinterpret_cast<int *>(raw + l.abort) + 1;
     sm.src = reinterpret_cast<SrcEntry *>(raw + l.src);
     sm.sstart = reinterpret_cast<int *>(raw + l.sstart);
     return sm;
