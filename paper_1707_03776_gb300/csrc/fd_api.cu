@@ -60,6 +60,10 @@ struct fd_operator {
     void *conv_res;        // Laplace: device {int64 steps, double r, double sum}
     // stencil-kernel timing (fd_operator_profile)
     std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
+    // receiver interpolation beside the grid update (tiled path): a side
+    // stream and the two events that order it with the operator's stream
+    cudaStream_t side;
+    cudaEvent_t ev_u, ev_rec;
     int64_t prof_max;
     int64_t prof_used;
 };
@@ -491,6 +495,12 @@ static void release(fd_operator *op)
     if (!op) return;
     if (op->conv_res) cudaFreeAsync(op->conv_res, op->stream);
     profile_clear(op);
+    if (op->side) {
+        cudaStreamSynchronize(op->side);
+        cudaStreamDestroy(op->side);
+    }
+    if (op->ev_u) cudaEventDestroy(op->ev_u);
+    if (op->ev_rec) cudaEventDestroy(op->ev_rec);
     if (op->c) cudaFreeAsync(op->c, op->stream);
     if (op->d) cudaFreeAsync(op->d, op->stream);
     if (op->status) cudaFreeAsync(op->status, op->stream);
@@ -557,6 +567,8 @@ extern "C" fd_status fd_operator_create(const fd_op_desc *desc, fd_operator **ou
     op->prof_used = 0;
     op->want_k = 0;
     op->want_sweep = 0;
+    op->side = nullptr;
+    op->ev_u = op->ev_rec = nullptr;
     op->jac_wr = op->jac_wc = 0.0f;
     op->conv_res = nullptr;
     std::memset(&op->coef, 0, sizeof op->coef);
@@ -690,6 +702,26 @@ static fd_status prepare_coefficients(fd_operator *op, double dt)
     return FD_OK;
 }
 
+// Receivers of step n read u^n while the update of step n writes the other
+// slot, so the interpolation runs on a side stream beside the update; the
+// operator's stream waits for it before the next update (which overwrites
+// u^n) and at the end of the call.
+static cudaError_t interpolate_beside(fd_operator *op, const float *u, float *rec_row)
+{
+    cudaError_t e = cudaSuccess;
+    if (!op->side) {
+        e = cudaStreamCreateWithFlags(&op->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&op->ev_u, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&op->ev_rec, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaEventRecord(op->ev_u, op->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(op->side, op->ev_u, 0);
+    if (e == cudaSuccess) e = launch_interpolate(op->rec->dev, u, rec_row, op->side);
+    if (e == cudaSuccess) e = cudaEventRecord(op->ev_rec, op->side);
+    return e;
+}
+
 extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt)
 {
     if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: null operator");
@@ -754,10 +786,11 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                     op->launches += 1;
                 }
             } else {
-                // receivers: a small kernel reading u^n; sources: fused into
-                // the tiled kernel when the per-tile lists fit in shared memory
+                // receivers: a small kernel reading u^n, beside the update;
+                // sources: fused into the tiled kernel when the per-tile
+                // lists fit in shared memory
                 if (rec_row) {
-                    FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
+                    FD_CUDA(interpolate_beside(op, u, rec_row), "interpolate");
                     op->launches += 1;
                 }
                 FD_CUDA(profile_mark(op, 0), "profile");
@@ -765,6 +798,7 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                         "acoustic step");
                 FD_CUDA(profile_mark(op, 1), "profile");
                 op->launches += 1;
+                if (rec_row) FD_CUDA(cudaStreamWaitEvent(st, op->ev_rec, 0), "interpolate");
                 if (src_row && !op->tma.has_src) {
                     FD_CUDA(launch_inject(op->src->dev, op->c, src_row, up, st), "inject");
                     op->launches += 1;
