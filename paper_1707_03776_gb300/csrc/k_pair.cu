@@ -46,7 +46,6 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <vector>
 
 #include "fd_internal.h"

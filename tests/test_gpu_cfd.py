@@ -147,6 +147,25 @@ def test_laplace_convergence_loop(flags, shape):
     assert np.all(got[0] == 0.0)
 
 
+@pytest.mark.parametrize("shape", [(31, 31), (120, 70)])
+def test_laplace_stops_at_max_iter(shape):
+    """A loop cut off by max_iter before the criterion: the sweeps done, the
+    field and the last r (formed from the final two sums) against the oracle;
+    then zero sweeps leave everything as it was."""
+    from paper_1707_03776_gb300 import fd
+    cfg = wl.laplace_config(nx=shape[0], ny=shape[1])
+    run = Run2D(fd.FD_LAPLACE_JACOBI, 2, cfg["p0"], cfg["spacing"])
+    it, r = run.op.converge(0, 37, cfg["tol"])
+    ref, it_ref, r_ref = oracle.laplace(cfg["p0"], cfg["spacing"], cfg["tol"], 37, precision="f32")
+    assert it == it_ref == 37 and r > cfg["tol"]
+    assert abs(r - r_ref) <= 1e-4 * r_ref
+    got = run.u.at(it).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    it0, r0 = run.op.converge(37, 0, cfg["tol"])
+    assert it0 == 0
+    np.testing.assert_array_equal(run.u.at(37).cpu().numpy(), got)
+
+
 def test_diffusion_time_blocks_agree_bitwise():
     from paper_1707_03776_gb300 import fd
     cfg = wl.diffusion_ring()
