@@ -584,7 +584,7 @@ def bench_learned(n=128, nt=2000):
     seeded layered models, evaluated on an unseen layered model on a 256^3-
     equivalent domain (128^3 coarse, 255^3 fine nodes) for 2000 coarse steps.
     Receiver-trace errors are relative to the plain fine-grid run (the
-    judge); the plain coarse grid at SO 4/8/16 shows what the spatial order
+    reference); the plain coarse grid at SO 4/8/16 shows what the spatial order
     alone buys at 20 m.  Wall times include every launch of the run (the
     network, the coarse update, the correction)."""
     import numpy as np
