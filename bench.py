@@ -618,6 +618,18 @@ def bench_learned(n=128, nt=2000):
     op.run(20)
     lr_tr, t_learned = timed(lambda: op.run().cpu().numpy())
     err = closure.trace_error(lr_tr, ref)
+    # the same comparison with a 24-cell sponge: with the thin 8-cell sponge
+    # the traces are dominated by boundary reverberations, which differ
+    # between the grids; the thick sponge leaves the interior propagation
+    cfg24 = wl.closure_config(n, nt, seed=1001, src="surface", sponge=24)
+    fine24 = closure.FineReference(cfg24)
+    ref24 = fine24.run().cpu().numpy()
+    del fine24
+    op24 = closure.ClosureOperator(cfg24, net)
+    thick = {"sponge_cells": 24,
+             "trace_rel_err_plain_coarse_SO4": closure.trace_error(op24.run(learned=False).cpu().numpy(), ref24),
+             "trace_rel_err_learned": closure.trace_error(op24.run().cpu().numpy(), ref24)}
+    del op24
     # the network alone: CUDA events around its launches
     st = torch.cuda.current_stream()
     for _ in range(3):
@@ -654,7 +666,7 @@ def bench_learned(n=128, nt=2000):
         "network forward on 32^3 points, numpy FP64")
     return {"workload": "closure_coarse%d^3_20m_so4_fine%d^3_10m_so16_nt%d_layered" % (n, 2 * n - 1, nt),
             "unit": "s per modelled shot; trace errors relative to the fine grid",
-            "trace_rel_err_learned": err, "trace_rel_err_plain_coarse": plain,
+            "trace_rel_err_learned": err, "trace_rel_err_plain_coarse": plain, "thick_sponge_check": thick,
             "s_learned": t_learned, "s_fine_grid": t_fine,
             "learned_vs_fine_time": t_learned / t_fine,
             "train": {"s": t_train, "samples": data.n, "models": 128, "iters": 800, "rho": net.rho,
