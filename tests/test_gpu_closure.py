@@ -344,8 +344,11 @@ def test_closure_rollout_parity():
 def test_training_lowers_loss_and_trace_error():
     """Training on 32 layered-model runs lowers the one-step loss tenfold, and the
     trained closure's receiver traces are closer to the fine grid's than the
-    plain coarse run's on an unseen model (smaller than the evaluation
-    workload; the full-size numbers come from bench.py)."""
+    plain coarse run's on an unseen model of the training configuration (8-cell
+    sponge; smaller than the evaluation workload).  This checks that training
+    works end to end on the GPU kernels; the gain it measures lies mostly in
+    the boundary region (bench.py's learned row also compares with a 24-cell
+    sponge, where it vanishes)."""
     _torch()
     from paper_1707_03776_gb300 import closure, workloads as wl
     net, data, hist = closure.train_default(count=32, n_coarse=64, nt=600, iters=800, log_every=100)
