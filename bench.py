@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    p.add_argument("--rows", default="diffusion,convection,laplace,gradient,batched,learned,two_step",
+    p.add_argument("--rows", default="space_orders,diffusion,convection,laplace,gradient,batched,learned,two_step",
                    help="secondary rows to run (comma-separated)")
     p.add_argument("--plain", action="store_true", help="plain kernels instead of the tiled ones")
     p.add_argument("--tiling", default="", help="rows,stages of the tiled kernel (default: autotuned)")
@@ -530,6 +530,44 @@ def bench_batched(nshots=64, nt=800, plain_shots=8):
             "launches_per_step": 1, "window_points": pts / nt}
 
 
+def bench_space_orders(n=512, nt=100, reps=3, orders=(2, 4, 8, 12, 16)):
+    """The 512^3 forward workload (source, 10 201 receivers, sponge) at every
+    space order the method covers: time per step of the whole run, the grid
+    update's own time from CUDA events on its launches and its fraction of the
+    measured HBM bandwidth at 20 bytes per point, and one step of the FP32
+    oracle on the host cores beside it."""
+    import torch
+    import oracle
+    from paper_1707_03776_gb300 import fd
+    from paper_1707_03776_gb300 import workloads as wl
+    from paper_1707_03776_gb300.modeling import AcousticModel
+    peak, kind = measured_peak_hbm()
+    out = {"workload": "acoustic3d_%d^3_nt%d_1src_101x101rec_sponge40" % (n, nt), "peak_kind": kind}
+    for so in orders:
+        cfg = wl.acoustic_config(n=n, space_order=so, nt=nt)
+        model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], so, cfg["src_coords"], cfg["rec_coords"],
+                              nt)
+        model.load(cfg["m"], cfg["eta"], cfg["src_trace"])
+        model.run(cfg["dt"])
+        model.op.sync()
+        model.op.profile(reps * nt)
+        ms = _time_runs(lambda: model.run(cfg["dt"]), reps, warmup=0) / nt
+        model.op.sync()
+        k_ms, k_n = model.op.profile_read()
+        kms = k_ms / k_n if k_n else None
+        rows, stages, ctas = fd.fd_operator_get_tiling(model.op.handle)
+        v, el = oracle_sample(cfg, so, 1)
+        out["SO%d" % so] = {
+            "ms_per_step": ms, "GPts_per_s": float(n) ** 3 / (ms * 1e-3) / 1e9, "kernel_ms": kms,
+            "roofline_frac": (BYTES_PER_POINT * float(n) ** 3 / (kms * 1e-3) / 1e9 / peak) if kms else None,
+            "tiling": {"rows_per_tile": rows, "prefetch_planes": stages, "ctas": ctas},
+            "cpu_oracle": {"value": v, "unit": "GPts/s", "cores": oracle.num_threads(), "s": el,
+                           "sample": "1 step, FP32"}}
+        del model
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_two_step(n=512, so=8, nt=200, reps=3):
     """Temporal blocking of the grid update: the headline forward workload
     (512^3 SO8, source and receivers) run with one and with two time steps
@@ -807,7 +845,7 @@ def run_ours(args):
     if rank == 0 and not args.no_rows:
         fns = {"diffusion": bench_diffusion, "convection": bench_convection, "laplace": bench_laplace,
                "gradient": bench_gradient, "batched": bench_batched, "learned": bench_learned,
-               "two_step": bench_two_step}
+               "two_step": bench_two_step, "space_orders": bench_space_orders}
         rows = {name: fns[name]() for name in args.rows.split(",") if name in fns}
 
     if rank == 0:
