@@ -172,8 +172,9 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     // (the 2M halo rows of a box cost about twice an interior row: TMA
     // traffic served from L2 and the barrier wait for it), with every tile of
     // one wave resident at once.  Two or more CTAs sharing an SM hide each
-    // other's per-plane barrier waits, worth a factor 1.5 (measured on 512^3
-    // SO4/8/16 sweeps of tile height and depth).  Ties go to taller tiles.
+    // other's per-plane barrier waits, worth a factor 1.5 for M >= 2 (at SO2
+    // one CTA of tall tiles per SM measured best; sweeps of tile height and
+    // depth at 128^3-512^3, SO 2-16).  Ties go to taller tiles.
     // The d0 chunk count kz multiplies the CTAs only for grids whose columns
     // alone leave SMs idle (up to the resident slots of all SMs); a chunk
     // costs its planes plus the 2M it loads before its first output plane
@@ -192,7 +193,7 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
         const long long waves = (per_sm + occ - 1) / occ;
         const double planes = (double)((a.n0 + kz - 1) / kz) + 0.35 * 2 * M;
         const long long resident = per_sm < occ ? per_sm : occ;
-        const double overlap = resident >= 2 ? 1.5 : 1.0;
+        const double overlap = resident >= 2 && M >= 2 ? 1.5 : 1.0;
         return (double)waves * occ * (rows_max + 4.0 * M) * planes * (per_sm > occ ? 1.0 : (double)per_sm / occ) /
                overlap;
     };
