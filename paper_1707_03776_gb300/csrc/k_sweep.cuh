@@ -293,6 +293,10 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
 
     int j = 0;
     bool ok = true, stop = false;
+    // at high orders the d0 queue shift (2M+1 float4 moves per plane) is a
+    // large share of the instructions: unrolling two planes lets them be
+    // renamed instead (measured: SO12/16 about 5 % faster, SO8 1.4 % slower)
+#pragma unroll(M >= 6 ? 2 : 1)
     for (; j < J; j++) {
         if (tid == 0 && j + P < J) issue(j + P);
         ok = wait_u(j) && ok;
