@@ -743,6 +743,10 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
         if (cs != FD_OK) return cs;
         const int sweep = plain ? 1 : acoustic_steps_per_sweep(op);
         const bool has_rec = op->rec && op->rec->npoint > 0, has_src = op->src && op->src->npoint > 0;
+        // receivers beside the update only for runs of many steps: a call of
+        // one step has nothing to overlap and would pay the two cross-stream
+        // dependencies per step (a step-by-step adjoint, for instance)
+        const bool beside = nt >= 16;
         for (int64_t q = 0; q < nt; q++) {
             int64_t n = reverse ? t0 + nt - 1 - q : t0 + q;
             int cur = (int)((reverse ? n + 1 : n) & 1);
@@ -790,7 +794,10 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                 // sources: fused into the tiled kernel when the per-tile
                 // lists fit in shared memory
                 if (rec_row) {
-                    FD_CUDA(interpolate_beside(op, u, rec_row), "interpolate");
+                    if (beside)
+                        FD_CUDA(interpolate_beside(op, u, rec_row), "interpolate");
+                    else
+                        FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
                     op->launches += 1;
                 }
                 FD_CUDA(profile_mark(op, 0), "profile");
@@ -798,7 +805,7 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                         "acoustic step");
                 FD_CUDA(profile_mark(op, 1), "profile");
                 op->launches += 1;
-                if (rec_row) FD_CUDA(cudaStreamWaitEvent(st, op->ev_rec, 0), "interpolate");
+                if (rec_row && beside) FD_CUDA(cudaStreamWaitEvent(st, op->ev_rec, 0), "interpolate");
                 if (src_row && !op->tma.has_src) {
                     FD_CUDA(launch_inject(op->src->dev, op->c, src_row, up, st), "inject");
                     op->launches += 1;

@@ -107,6 +107,10 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
 cudaError_t launch_acoustic_tma(const TmaPlan &plan, int M, const Geom &g, const Coef &cf,
                                 int cur, int *status, const float *src_row, cudaStream_t st);
 
+// CTAs of the tiled kernel of half-width M and depth P resident per SM with
+// `threads` threads and `smem` bytes of dynamic shared memory (0 if none).
+int tma_occupancy(int M, int P, int threads, size_t smem);
+
 // Tensor map of a 3D field of the tiling `a` with a box of box_w x box_h x 1.
 fd_status tma_encode_3d(CUtensorMap *map, float *base, const TileArgs &a, int box_w, int box_h);
 

@@ -386,14 +386,25 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
     std::vector<int> off;
     int max_s = 0;
     fused_corner_lists(a, src, all, off, max_s);
-    // the tile's corners are staged in shared memory: lower the prefetch depth
-    // if that is what it takes, else leave injection to its own kernel
-    while (plan.stages > kMinStages && tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, max_s) > plan.smem_max)
-        plan.stages--;
-    if (tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, max_s) > plan.smem_max) {
-        plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, 0);
-        return FD_OK;
+    // The tile's corners are staged in shared memory.  Staging them must
+    // keep the CTAs per SM the tiling places (a second wave costs far more
+    // than the atomic injection kernel: a receiver lattice injected by the
+    // adjoint puts thousands of corners in one tile column), lowering the
+    // prefetch depth if that is what it takes; else injection keeps its own
+    // kernel.
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ctas = (long long)a.k1 * a.k2 * a.kz;
+    const int need = std::min<int>(tma_occupancy(M, plan.stages, plan.threads, plan.smem),
+                                   (int)((ctas + sms - 1) / sms));
+    int P = plan.stages;
+    for (; P >= kMinStages; P--) {
+        const size_t with = tma_smem_bytes(M, P, a.rows_max, a.n0, max_s);
+        if (with <= plan.smem_max && tma_occupancy(M, P, plan.threads, with) >= need) break;
     }
+    if (P < kMinStages) return FD_OK;
+    plan.stages = P;
     fd_status s = fused_upload(all, off, st, plan.fused, plan.fused_mem);
     if (s != FD_OK) return s;
     plan.has_src = true;
@@ -407,6 +418,23 @@ void tma_plan_tiling(const TmaPlan &plan, int *rows, int *stages, int *ctas)
     *rows = plan.ready ? plan.args.rows_max : 0;
     *stages = plan.ready ? plan.stages : 0;
     *ctas = plan.ready ? plan.args.k1 * plan.args.k2 * plan.args.kz : 0;
+}
+
+int tma_occupancy(int M, int P, int threads, size_t smem)
+{
+    int occ = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (M * 8 + P) {
+#define CASE(MM, PP)                                                                                      \
+    case MM * 8 + PP:                                                                                     \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, acoustic_tma_kernel<MM, PP>, threads, smem); \
+        break;
+#define CASES(MM) CASE(MM, 2) CASE(MM, 3) CASE(MM, 4)
+        CASES(1) CASES(2) CASES(3) CASES(4) CASES(5) CASES(6) CASES(7) CASES(8)
+#undef CASES
+#undef CASE
+    }
+    return e == cudaSuccess ? occ : 0;
 }
 
 static cudaError_t launch_maps(const TmaPlan &plan, int M, const Coef &cf, const CUtensorMap &map_cur,
