@@ -56,7 +56,8 @@ struct ClusterArgs {
     int halo;         // halo rows on each side: K*M (M when alone)
     int K;            // steps between exchanges
     int nctas;        // CTAs in the cluster
-    int tc, tr;       // threads along columns and rows
+    int tc, tr;       // threads along columns (float4 chunks when vec) and rows
+    int vec;          // SO2 diffusion: each thread updates 4 columns with 128-bit loads
 };
 
 struct RuleArgs {
@@ -299,7 +300,45 @@ __global__ void __launch_bounds__(kCThreads, 1)
             const int lo = max(-ext, -r0), hi = min(nr + ext, a.rows - r0);
             const float *src = buf[cur];
             float *dst = buf[cur ^ 1];
-            if (lane_on) {
+            if (RULE == kRuleDiffusion && M == 1 && a.vec) {
+                // 4 columns per thread: rows padded with 4 zero columns so
+                // every chunk is 16-byte aligned; the left and right
+                // neighbours come from the adjacent chunks (same arithmetic
+                // per point as apply_rule)
+                if (lane_on)
+                    for (int lr = lo + tr; lr < hi; lr += a.tr) {
+                        const int base = (lr + H) * W + a.hc;
+                        for (int c = 4 * tc; c < a.cols; c += 4 * a.tc) {
+                            const float *p = src + base + c;
+                            const float4 cu = *reinterpret_cast<const float4 *>(p);
+                            const float4 lf = *reinterpret_cast<const float4 *>(p - 4);
+                            const float4 rt = *reinterpret_cast<const float4 *>(p + 4);
+                            const float4 up = *reinterpret_cast<const float4 *>(p - W);
+                            const float4 dn = *reinterpret_cast<const float4 *>(p + W);
+                            const float uu[6] = {lf.w, cu.x, cu.y, cu.z, cu.w, rt.x};
+                            const float uv[4] = {up.x, up.y, up.z, up.w};
+                            const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+                            float o[4];
+#pragma unroll
+                            for (int i = 0; i < 4; i++) {
+                                const float u = uu[i + 1];
+                                float lap = ra.cf.centre * u;
+                                lap = fmaf(ra.cf.ax[2][1], uu[i] + uu[i + 2], lap);
+                                lap = fmaf(ra.cf.ax[1][1], uv[i] + dv[i], lap);
+                                o[i] = fmaf(ra.adt, lap, u);
+                            }
+                            float *d = dst + base + c;
+                            if (c + 3 < a.cols) {
+                                *reinterpret_cast<float4 *>(d) = make_float4(o[0], o[1], o[2], o[3]);
+                            } else {
+                                // the zero columns past the grid must stay zero
+#pragma unroll
+                                for (int i = 0; i < 4; i++)
+                                    if (c + i < a.cols) d[i] = o[i];
+                            }
+                        }
+                    }
+            } else if (lane_on) {
                 for (int lr = lo + tr; lr < hi; lr += a.tr) {
                     const int base = (lr + H) * W + a.hc;
                     const int gr = r0 + lr;
@@ -474,6 +513,13 @@ bool clusters_fit_rule(int rule, int M, int n, size_t smem)
     return false;
 }
 
+// SO2 diffusion runs the 4-column (float4) sweep
+bool cluster_vec(int rule, int M) { return rule == kRuleDiffusion && M == 1; }
+
+// zero columns on each side of a shared row, and the row pitch
+int cluster_hc(int rule, int M) { return cluster_vec(rule, M) ? 4 : M; }
+int cluster_width(int rule, int M, int cols) { return (cols + 2 * cluster_hc(rule, M) + 3) / 4 * 4; }
+
 ClusterArgs make_args(const ClusterPlan &p, const Geom &g)
 {
     ClusterArgs a;
@@ -482,11 +528,13 @@ ClusterArgs make_args(const ClusterPlan &p, const Geom &g)
     a.s1 = g.s1;
     a.nctas = p.nctas;
     a.strip = (a.rows + p.nctas - 1) / p.nctas;
-    a.hc = p.M;
-    a.width = (a.cols + 2 * a.hc + 3) / 4 * 4;
+    a.hc = cluster_hc(p.rule, p.M);
+    a.width = cluster_width(p.rule, p.M, a.cols);
     a.K = p.K;
     a.halo = p.halo;
-    a.tc = std::min(kCThreads, (a.cols + 31) / 32 * 32);
+    a.vec = cluster_vec(p.rule, p.M) ? 1 : 0;
+    const int units = a.vec ? (a.cols + 3) / 4 : a.cols;  // work items along a row
+    a.tc = std::min(kCThreads, (units + 31) / 32 * 32);
     a.tr = kCThreads / a.tc;
     return a;
 }
@@ -508,7 +556,7 @@ bool cluster_plan_build(int rule, int M, const Geom &g, int want_k, ClusterPlan 
     if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
     const int rows = (int)g.n[1], cols = (int)g.n[2];
     if (rows < 1 || cols < 1 || (rule == kRuleJacobi && (rows < 3 || cols < 3))) return false;
-    const int width = (cols + 2 * M + 3) / 4 * 4;
+    const int width = cluster_width(rule, M, cols);
     const long long pts = (long long)rows * cols;
     int chosen = 0;
     for (int n : {1, 2, 4, 8, 16}) {
