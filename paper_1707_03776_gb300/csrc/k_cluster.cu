@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
             const int lo = max(-ext, -r0), hi = min(nr + ext, a.rows - r0);
             const float *src = buf[cur];
             float *dst = buf[cur ^ 1];
-            if (RULE == kRuleDiffusion && M == 1 && a.vec) {
+            if ((RULE == kRuleDiffusion || RULE == kRuleUpwind) && M == 1 && a.vec) {
                 // 4 columns per thread: rows padded with 4 zero columns so
                 // every chunk is 16-byte aligned; the left and right
                 // neighbours come from the adjacent chunks (same arithmetic
@@ -322,10 +322,14 @@ __global__ void __launch_bounds__(kCThreads, 1)
 #pragma unroll
                             for (int i = 0; i < 4; i++) {
                                 const float u = uu[i + 1];
-                                float lap = ra.cf.centre * u;
-                                lap = fmaf(ra.cf.ax[2][1], uu[i] + uu[i + 2], lap);
-                                lap = fmaf(ra.cf.ax[1][1], uv[i] + dv[i], lap);
-                                o[i] = fmaf(ra.adt, lap, u);
+                                if (RULE == kRuleDiffusion) {
+                                    float lap = ra.cf.centre * u;
+                                    lap = fmaf(ra.cf.ax[2][1], uu[i] + uu[i + 2], lap);
+                                    lap = fmaf(ra.cf.ax[1][1], uv[i] + dv[i], lap);
+                                    o[i] = fmaf(ra.adt, lap, u);
+                                } else {
+                                    o[i] = u - ra.nux * (u - uv[i]) - ra.nuy * (u - uu[i]);
+                                }
                             }
                             float *d = dst + base + c;
                             if (c + 3 < a.cols) {
@@ -513,8 +517,8 @@ bool clusters_fit_rule(int rule, int M, int n, size_t smem)
     return false;
 }
 
-// SO2 diffusion runs the 4-column (float4) sweep
-bool cluster_vec(int rule, int M) { return rule == kRuleDiffusion && M == 1; }
+// SO2 diffusion and the upwind rule run the 4-column (float4) sweep
+bool cluster_vec(int rule, int M) { return (rule == kRuleDiffusion || rule == kRuleUpwind) && M == 1; }
 
 // zero columns on each side of a shared row, and the row pitch
 int cluster_hc(int rule, int M) { return cluster_vec(rule, M) ? 4 : M; }
