@@ -214,15 +214,24 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def kernel_source_sha():
+    """First 16 hex digits of the SHA-256 of the grid-update kernel's source:
+    k_tma.cu followed by the column sweep it instantiates, k_sweep.cuh."""
+    h = hashlib.sha256()
+    for f in ("k_tma.cu", "k_sweep.cuh"):
+        with open(os.path.join(ROOT, "paper_1707_03776_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(so):
     """DRAM bytes per launch of the grid-update kernel from the committed ncu
     summary, if it was taken on the kernel source as it is now."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1707_03776_gb300", "csrc", "k_tma.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
         entry = rec.get("so%d" % so)
         if entry and entry.get("source_sha") == sha:
             return float(entry["bytes_per_launch_512"])

@@ -333,23 +333,43 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
                 const float umv[4] = {um4.x, um4.y, um4.z, um4.w};
                 const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
                 const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
-                float res[4];
+                // Laplacian of the 4 points as two pairs, with the packed
+                // FP32 instructions (two lanes per issue).  Each lane does
+                // the same operations in the same order as the scalar form
+                // centre*u, then per k: ax2*(d2 pair) + ax1*(d1 pair) +
+                // ax0*(d0 pair), so the result is bitwise unchanged.
+                float lapv[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const float u = row[4 * HV + i];
-                    float lap = cf.centre * u;
+                for (int h = 0; h < 2; h++) {
+                    const int c = 4 * HV + 2 * h;
+                    float2 lap = __fmul2_rn(make_float2(cf.centre, cf.centre), make_float2(row[c], row[c + 1]));
 #pragma unroll
                     for (int k = 1; k <= M; k++) {
                         const float4 lo = q[M - k];
                         const float4 hi = q[M + k];
-                        const float s2 = row[4 * HV + i - k] + row[4 * HV + i + k];
-                        const float s1 = (&cm[k].x)[i] + (&cp[k].x)[i];
-                        const float s0 = (&lo.x)[i] + (&hi.x)[i];
-                        lap = fmaf(cf.ax[2][k], s2, lap);
-                        lap = fmaf(cf.ax[1][k], s1, lap);
-                        lap = fmaf(cf.ax[0][k], s0, lap);
+                        // an odd k puts the d2 pair across a 64-bit register
+                        // boundary: two scalar adds then, not a packed one
+                        const float2 s2 =
+                            (k % 2 == 0)
+                                ? __fadd2_rn(make_float2(row[c - k], row[c - k + 1]),
+                                             make_float2(row[c + k], row[c + k + 1]))
+                                : make_float2(row[c - k] + row[c + k], row[c + 1 - k] + row[c + 1 + k]);
+                        const float2 s1 = h ? __fadd2_rn(make_float2(cm[k].z, cm[k].w), make_float2(cp[k].z, cp[k].w))
+                                            : __fadd2_rn(make_float2(cm[k].x, cm[k].y), make_float2(cp[k].x, cp[k].y));
+                        const float2 s0 = h ? __fadd2_rn(make_float2(lo.z, lo.w), make_float2(hi.z, hi.w))
+                                            : __fadd2_rn(make_float2(lo.x, lo.y), make_float2(hi.x, hi.y));
+                        lap = __ffma2_rn(make_float2(cf.ax[2][k], cf.ax[2][k]), s2, lap);
+                        lap = __ffma2_rn(make_float2(cf.ax[1][k], cf.ax[1][k]), s1, lap);
+                        lap = __ffma2_rn(make_float2(cf.ax[0][k], cf.ax[0][k]), s0, lap);
                     }
-                    res[i] = 2.0f * u - umv[i] + cv[i] * lap - dv[i] * (u - umv[i]);
+                    lapv[2 * h] = lap.x;
+                    lapv[2 * h + 1] = lap.y;
+                }
+                float res[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float u = row[4 * HV + i];
+                    res[i] = 2.0f * u - umv[i] + cv[i] * lapv[i] - dv[i] * (u - umv[i]);
                 }
                 if (nsrc > 0) {
                     // source injection at the corners this thread owns on plane ja
