@@ -82,7 +82,9 @@ __device__ __forceinline__ float apply_rule(const float *__restrict__ src, int a
         return fmaf(ra.adt, lap, u);
     } else if (RULE == kRuleUpwind) {
         const float u = src[at];
-        return u - ra.nux * (u - src[at - W]) - ra.nuy * (u - src[at - 1]);
+        // u - nux (u - u_up) - nuy (u - u_left), as two explicit FMAs so that
+        // the packed 4-column sweep can repeat it bit for bit
+        return fmaf(-ra.nuy, u - src[at - 1], fmaf(-ra.nux, u - src[at - W], u));
     } else {
         const int cc = c == 0 ? 1 : (c == a.cols - 1 ? a.cols - 2 : c);
         const int q = at + (cc - c);
@@ -316,20 +318,34 @@ __global__ void __launch_bounds__(kCThreads, 1)
                             const float4 up = *reinterpret_cast<const float4 *>(p - W);
                             const float4 dn = *reinterpret_cast<const float4 *>(p + W);
                             const float uu[6] = {lf.w, cu.x, cu.y, cu.z, cu.w, rt.x};
-                            const float uv[4] = {up.x, up.y, up.z, up.w};
-                            const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+                            // the 4 points as two pairs on the packed FP32
+                            // instructions, each lane in the scalar order of
+                            // apply_rule (bitwise the same results)
                             float o[4];
 #pragma unroll
-                            for (int i = 0; i < 4; i++) {
-                                const float u = uu[i + 1];
+                            for (int h = 0; h < 2; h++) {
+                                const float2 u2 = h ? make_float2(cu.z, cu.w) : make_float2(cu.x, cu.y);
+                                const float2 up2 = h ? make_float2(up.z, up.w) : make_float2(up.x, up.y);
+                                float2 r2;
                                 if (RULE == kRuleDiffusion) {
-                                    float lap = ra.cf.centre * u;
-                                    lap = fmaf(ra.cf.ax[2][1], uu[i] + uu[i + 2], lap);
-                                    lap = fmaf(ra.cf.ax[1][1], uv[i] + dv[i], lap);
-                                    o[i] = fmaf(ra.adt, lap, u);
+                                    const float2 dn2 = h ? make_float2(dn.z, dn.w) : make_float2(dn.x, dn.y);
+                                    // left + right straddles a 64-bit register pair: scalar adds
+                                    const float2 s2 = make_float2(uu[2 * h] + uu[2 * h + 2], uu[2 * h + 1] + uu[2 * h + 3]);
+                                    float2 lap = __fmul2_rn(make_float2(ra.cf.centre, ra.cf.centre), u2);
+                                    lap = __ffma2_rn(make_float2(ra.cf.ax[2][1], ra.cf.ax[2][1]), s2, lap);
+                                    lap = __ffma2_rn(make_float2(ra.cf.ax[1][1], ra.cf.ax[1][1]), __fadd2_rn(up2, dn2), lap);
+                                    r2 = __ffma2_rn(make_float2(ra.adt, ra.adt), lap, u2);
                                 } else {
-                                    o[i] = u - ra.nux * (u - uv[i]) - ra.nuy * (u - uu[i]);
+                                    // the two FMAs of apply_rule's upwind form; x - y
+                                    // is x + (-y) exactly
+                                    const float2 lf2 = make_float2(uu[2 * h], uu[2 * h + 1]);
+                                    const float2 dx = __fadd2_rn(u2, make_float2(-up2.x, -up2.y));
+                                    const float2 dy = __fadd2_rn(u2, make_float2(-lf2.x, -lf2.y));
+                                    const float2 a = __ffma2_rn(make_float2(-ra.nux, -ra.nux), dx, u2);
+                                    r2 = __ffma2_rn(make_float2(-ra.nuy, -ra.nuy), dy, a);
                                 }
+                                o[2 * h] = r2.x;
+                                o[2 * h + 1] = r2.y;
                             }
                             float *d = dst + base + c;
                             if (c + 3 < a.cols) {

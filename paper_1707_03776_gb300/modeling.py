@@ -50,7 +50,9 @@ class AcousticModel:
         self.op.bind("eta", self.eta)
 
     def autotune(self, dt, nsteps=20):
-        """Pick the fastest tiling on this model's data (leaves u zeroed)."""
+        """Pick the fastest tiling on this model's data (leaves u zeroed);
+        the trial runs take at most the model's nt steps."""
+        nsteps = max(1, min(int(nsteps), self.nt))
         for s in self.u.slots:
             s.zero_()
         best = fd.fd_operator_autotune(self.op.handle, 0, nsteps, dt)
