@@ -188,7 +188,9 @@ __global__ void convection_plain_kernel(Geom g, float nux, float nuy, const floa
     const float uc = u[at];
     const float ux = i1 > 0 ? u[at - g.s1] : 0.0f;
     const float uy = i2 > 0 ? u[at - 1] : 0.0f;
-    out[at] = uc - nux * (uc - ux) - nuy * (uc - uy);
+    // two explicit FMAs, in the order the cluster kernel uses, so that both
+    // paths give the same bits
+    out[at] = fmaf(-nuy, uc - uy, fmaf(-nux, uc - ux, uc));
 }
 
 __device__ __forceinline__ void add_block_sum(double v, double *sum)

@@ -4,8 +4,8 @@ small-grid cluster kernels, on the GPU against the oracle.
 Fields are FP32 on both sides (the oracle's FP32 loop nest, no FMA); the GPU
 contracts to FMA, so single steps agree to a few ulp and runs to 1e-5 of the
 field's maximum.  The cluster kernels compute the same per-point arithmetic
-for every number of steps between exchanges, so those results agree bit for
-bit.  The convergence loop sums |p| in FP64 on both sides and stops at the
+for every number of steps between exchanges, and in the same order as the
+plain per-step kernels, so those results agree bit for bit.  The convergence loop sums |p| in FP64 on both sides and stops at the
 same sweep unless the two r straddle tol within their FP32 difference.
 """
 import numpy as np
@@ -71,6 +71,28 @@ def test_convection_parity_and_time_blocks(shape):
     plain = Run2D(fd.FD_CONVECTION_UPWIND, 1, u0, h, a=c, flags=fd.FD_FLAG_PLAIN_KERNELS)
     last, _ = plain.run(0, 23, dt)
     assert np.abs(last - ref).max() <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("kind,so", [("diffusion", 2), ("diffusion", 4), ("convection", 1)])
+def test_cluster_and_plain_kernels_agree_bitwise(kind, so):
+    """One cluster launch for the whole run (K steps per exchange; at SO2 4
+    columns per thread on the paired FP32 instructions) and one launch of the
+    plain kernel per step do the same arithmetic per point in the same order,
+    so the fields agree bit for bit after many steps."""
+    from paper_1707_03776_gb300 import fd
+    if kind == "diffusion":
+        cfg = wl.diffusion_ring(courant=0.1)
+        args, a, dt, nt = (fd.FD_DIFFUSION_EULER, so, cfg["u0"], cfg["spacing"]), cfg["a"], cfg["dt"], 61
+    else:
+        u0, h, c, dt = _conv_case((83, 77), 3)
+        args, a, nt = (fd.FD_CONVECTION_UPWIND, 1, u0, h), c, 29
+    fast = Run2D(*args, a=a)
+    plain = Run2D(*args, a=a, flags=fd.FD_FLAG_PLAIN_KERNELS)
+    f_last, f_prev = fast.run(0, nt, dt)
+    p_last, p_prev = plain.run(0, nt, dt)
+    assert np.abs(f_last).max() > 0
+    np.testing.assert_array_equal(f_last, p_last)
+    np.testing.assert_array_equal(f_prev, p_prev)
 
 
 def test_convection_example_workload():
