@@ -148,7 +148,8 @@ __device__ __forceinline__ void update4(const float *pc, const float4 (&q)[QN], 
             lap = fmaf(cf.ax[1][k], s1, lap);
             lap = fmaf(cf.ax[0][k], s0, lap);
         }
-        res[i] = 2.0f * u - umv[i] + cv[i] * lap - dv[i] * (u - umv[i]);
+        // the tiled kernel's chain of three FMAs
+        res[i] = fmaf(-dv[i], u - umv[i], fmaf(cv[i], lap, fmaf(2.0f, u, -umv[i])));
     }
 }
 

@@ -124,7 +124,8 @@ __global__ void acoustic_plain_kernel(Geom g, Coef cf, const float *__restrict__
         float lap = laplacian_at<M, THREE_D>(g, cf, u, at, i0, i1, i2);
         float uc = u[at];
         float upv = up[at];
-        out[at] = 2.0f * uc - upv + c[at] * lap - d[at] * (uc - upv);
+        // three explicit FMAs (2u is exact), the chain the tiled kernels use
+        out[at] = fmaf(-d[at], uc - upv, fmaf(c[at], lap, fmaf(2.0f, uc, -upv)));
     }
 }
 

@@ -369,7 +369,9 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     const float u = row[4 * HV + i];
-                    res[i] = 2.0f * u - umv[i] + cv[i] * lapv[i] - dv[i] * (u - umv[i]);
+                    // 2u - u- + c Lu - d (u - u-) as three explicit FMAs (2u is
+                    // exact), the same chain in every acoustic kernel
+                    res[i] = fmaf(-dv[i], u - umv[i], fmaf(cv[i], lapv[i], fmaf(2.0f, u, -umv[i])));
                 }
                 if (nsrc > 0) {
                     // source injection at the corners this thread owns on plane ja
