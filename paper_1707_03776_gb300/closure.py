@@ -236,24 +236,24 @@ class Dataset:
     S_c(R u_f^n, R u_f^{n-1}) ('base'), the coarse model m, and the sample's
     feature scale s = RMS(R u_f^n)."""
 
-    def __init__(self, configs, steps):
+    def __init__(self, cases, steps):
         import torch
         steps = [int(n) for n in steps]
         if steps[0] < 1 or any(b - a < 2 for a, b in zip(steps, steps[1:])):
             raise ValueError("sample steps must start at >= 1 and be at least 2 apart")
         self.torch = torch
-        c0 = configs[0]["coarse"]
+        c0 = cases[0]["coarse"]
         self.shape = c0["shape"]
-        self.cgrid = fd.Grid(c0["shape"], c0["spacing"], configs[0]["origin"])
+        self.cgrid = fd.Grid(c0["shape"], c0["spacing"], cases[0]["origin"])
         ps = self.cgrid.padded_shape
-        ns = len(configs) * len(steps)
+        ns = len(cases) * len(steps)
         self.states = torch.zeros((ns, 4) + ps, dtype=torch.float32, device="cuda")  # prev, cur, next, base
-        self.models = torch.zeros((len(configs),) + ps, dtype=torch.float32, device="cuda")
+        self.models = torch.zeros((len(cases),) + ps, dtype=torch.float32, device="cuda")
         self.model_of = np.zeros(ns, dtype=np.int64)
         sumsq = torch.zeros(ns, dtype=torch.float32, device="cuda")
         st = _stream()
         k = 0
-        for mi, cfg in enumerate(configs):
+        for mi, cfg in enumerate(cases):
             cs = cfg["coarse"]
             self.models[mi, ..., : self.shape[2]].copy_(torch.from_numpy(cs["m"]))
             fine = FineReference(cfg, receivers=False)
