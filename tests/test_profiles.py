@@ -1,8 +1,10 @@
-"""The committed DRAM-traffic record of the grid-update kernel is consistent:
-read + write add up to the per-launch figure the bench reports, that figure
-is within a few per cent of the algorithmic 20 bytes per point (no wasted
-re-reads), and the bench uses it only while the kernel source is the one the
-counters were taken on."""
+"""The committed profiles.  The DRAM-traffic record of the grid-update kernel
+is consistent: read + write add up to the per-launch figure the bench
+reports, that figure is within a few per cent of the algorithmic 20 bytes per
+point (no wasted re-reads), and the bench uses it only while the kernel source
+is the one the counters were taken on.  Every ncu summary gives the command
+that produced it, which runs committed files only and keeps the GPU clocks
+unlocked (--clock-control none)."""
 import json
 import os
 import re
@@ -54,3 +56,32 @@ def test_bench_reports_traffic_only_for_the_source_it_was_taken_on(tmp_path, mon
 
     monkeypatch.setattr(bench.os.path, "join", join)
     assert bench.kernel_traffic(8) is None
+
+
+def _profile_commands():
+    out = {}
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)):
+        if f.endswith(".md"):
+            text = open(os.path.join(pdir, f)).read()
+            out[f] = re.findall(r"```\n(.*?)```", text, flags=re.S)
+    return out
+
+
+def test_every_profile_gives_a_command_that_runs_committed_files_only():
+    cmds = _profile_commands()
+    assert cmds
+    for f, blocks in cmds.items():
+        assert blocks, "%s has no command" % f
+        text = "\n".join(blocks).replace("\\\n", " ")
+        assert "_work" not in text and "gpurun" not in text, f
+        for line in text.splitlines():
+            for m in re.finditer(r"python (?:-m ([\w.]+)|([\w/]+\.py))", line):
+                if m.group(1):
+                    path = os.path.join(ROOT, *m.group(1).split(".")) + ".py"
+                else:
+                    path = os.path.join(ROOT, m.group(2))
+                assert os.path.isfile(path), (f, line)
+            for part in line.split("&&"):
+                if part.strip().startswith("ncu"):
+                    assert "--clock-control none" in part, (f, line)
