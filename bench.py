@@ -805,8 +805,8 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         # each step (one forward call: host model in, traces out) timed on its
-        # own; the median of three, because the host copies of one call vary
-        # with the load on a shared host
+        # own; the median of three, because the host-side part of a call (the
+        # copies and the launches) varies from call to call
         e_steps = 3
         model.forward(m_h, eta_h, src_h, cfg["dt"])  # warm
         barrier()
