@@ -810,17 +810,20 @@ def run_ours(args):
         e_steps = 3
         model.forward(m_h, eta_h, src_h, cfg["dt"])  # warm
         barrier()
-        els = []
+        els, phases = [], []
         for _ in range(e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            out = model.forward(m_h, eta_h, src_h, cfg["dt"])
+            ph = {}
+            out = model.forward(m_h, eta_h, src_h, cfg["dt"], timings=ph)
             torch.cuda.synchronize()
             els.append(max_over_ranks(time.perf_counter() - t0, world))
+            phases.append({k: round(v * 1e3, 3) for k, v in ph.items()})
         el = sorted(els)[len(els) // 2]
         e2e = {"value": whole_job_rate(pts, 1, world, el), "unit": "GPts/s",
                "h2d_bytes_per_step": model.h2d_bytes(), "d2h_bytes_per_step": model.d2h_bytes(),
                "steps": e_steps, "stat": "median of the steps", "s_per_step": els,
+               "host_phases_ms": phases,
                "api": "AcousticModel.forward (host pinned m, eta, wavelet -> host traces)"}
         assert out.shape[0] == args.nt
 

@@ -7,6 +7,8 @@ tables are set up once, runs the whole time loop through the C ABI and copies
 the receiver traces back.  Host tensors should be pinned for asynchronous
 copies.
 """
+import time
+
 import numpy as np
 
 from . import fd
@@ -67,11 +69,25 @@ class AcousticModel:
             s.zero_()
         self.op.apply(0, self.nt, dt)
 
-    def forward(self, m, eta, src_trace, dt):
-        """Host m, eta, src trace in -> host receiver traces [nt, nrec] out."""
+    def forward(self, m, eta, src_trace, dt, timings=None):
+        """Host m, eta, src trace in -> host receiver traces [nt, nrec] out.
+
+        With a dict `timings`, the host-side phases of the call are added to
+        it in seconds (no extra synchronisation): "load" (the copies in and
+        the min(m) check, which waits for them), "launch" (enqueueing the
+        time loop and the copy back) and "wait" (until the traces are on the
+        host)."""
+        t0 = time.perf_counter()
         self.load(m, eta, src_trace)
+        t1 = time.perf_counter()
         self.run(dt)
         self.rec_host.copy_(self.rec.data[:, : self.rec.npoint], non_blocking=True)
+        t2 = time.perf_counter()
         self.torch.cuda.current_stream().synchronize()
         self.op.sync()
+        if timings is not None:
+            t3 = time.perf_counter()
+            timings["load"] = t1 - t0
+            timings["launch"] = t2 - t1
+            timings["wait"] = t3 - t2
         return self.rec_host
