@@ -498,13 +498,21 @@ fd_status fd_cnn_adam(float *params, const float *grads, float *m1, float *m2, i
  *   dev_out    device FP32 [npoint]
  *   cuda_stream  cudaStream_t the copy and the kernel are enqueued on
  * The interpolation table lives in one static device array of
- * FD_NOALLOC_MAX_POINTS entries (40 bytes each, 2.6 MB) that every GPU loading
- * the library holds until the process exits; the call writes the entries it
- * uses (nothing in it needs to start at zero) and calls no allocating
- * routine.  All calls on a device share that array and it keeps the last
- * call's table: calls whose work overlaps on the GPU (e.g. on two streams)
- * race.  The first call on a device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * FD_NOALLOC_MAX_POINTS entries (40 bytes each, 2.6 MB) that every GPU using
+ * this call holds until the process exits; the call writes the entries it
+ * uses (nothing in it needs to start at zero).  All calls on a device share
+ * that array and it keeps the last call's table: calls whose work overlaps on
+ * the GPU (e.g. on two streams) race.
+ * Set-up: CUDA loads the library's modules lazily, so the FIRST call on a
+ * device, with that device current, loads the module holding the array --
+ * which allocates the array on that device and may synchronise it -- looks
+ * up its device address and loads the interpolation kernel.  A call with
+ * npoint = 0 does only this set-up (grid and pointers may then be NULL):
+ * make it at start-up, while device memory can still be had, and before any
+ * stream capture.  After it, calls on that device call no allocating routine.
+ * The table reaches the device by cudaMemcpyAsync from a static pageable host
+ * buffer: the call waits on the host for the stream's earlier work, and
+ * concurrent callers are serialised by a lock.
  * Errors: FD_ERR_INVALID_ARG (npoint > FD_NOALLOC_MAX_POINTS or < 0, null
  * pointers), FD_ERR_OUT_OF_DOMAIN, FD_ERR_CUDA. */
 fd_status fd_interpolate_noalloc(const fd_grid *grid, int npoint, const double *coords,

@@ -97,9 +97,9 @@ static fd_status cuda_error(cudaError_t e, const char *what)
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Row pitch (elements) of the contiguous axis.
-static int64_t row_pitch(const fd_grid &g) { return round_up(g.shape[g.ndim - 1], 8); }
+int64_t row_pitch(const fd_grid &g) { return round_up(g.shape[g.ndim - 1], 8); }
 
-static void layout_of(const fd_grid &g, int64_t *padded, int64_t *strides)
+void layout_of(const fd_grid &g, int64_t *padded, int64_t *strides)
 {
     int64_t S = row_pitch(g);
     if (g.ndim == 3) {
@@ -109,6 +109,60 @@ static void layout_of(const fd_grid &g, int64_t *padded, int64_t *strides)
         padded[0] = g.shape[0]; padded[1] = S;
         strides[0] = S; strides[1] = 1;
     }
+}
+
+// Linear offset of corner k (bit a of k: +1 along axis a) from a point's
+// lowest corner, in the slot layout; corners past 2^ndim are 0.
+void corner_offsets(const fd_grid &g, int64_t off[8])
+{
+    int64_t padded[3], st[3];
+    layout_of(g, padded, st);
+    for (int k = 0; k < 8; k++) {
+        off[k] = 0;
+        if (k < (1 << g.ndim))
+            for (int a = 0; a < g.ndim; a++) off[k] += ((k >> a) & 1) * st[a];
+    }
+}
+
+// The linear-interpolation table of the paper's PointData (the weights of
+// `interpolate` and `inject`): per point the slot-layout index of its lowest
+// corner and the 2^ndim products of (1 - f) or f per axis, with
+// s = (x - origin)/h, i = floor(s) clamped to n - 2 (a point on the upper
+// face takes weight 1 on the last node) and f = s - i, all in FP64 and each
+// weight rounded once to FP32 (unused corners 0).  Points outside
+// [origin, origin + (n-1) h] are rejected.
+fd_status linear_table(const fd_grid &g, int npoint, const double *coords, int64_t *base, float *weight,
+                       const char *who)
+{
+    const int ndim = g.ndim;
+    int64_t padded[3], st[3];
+    layout_of(g, padded, st);
+    for (int p = 0; p < npoint; p++) {
+        int64_t lin = 0;
+        double frac[3] = {0, 0, 0};
+        for (int a = 0; a < ndim; a++) {
+            double x = coords[(int64_t)p * ndim + a];
+            double s = (x - g.origin[a]) / g.spacing[a];
+            double top = (double)(g.shape[a] - 1);
+            if (!(s >= 0.0) || !(s <= top))
+                return set_error(FD_ERR_OUT_OF_DOMAIN, "%s: point %d coordinate %d = %g outside [%g, %g]", who, p,
+                                 a, x, g.origin[a], g.origin[a] + top * g.spacing[a]);
+            int64_t i = (int64_t)std::floor(s);
+            if (i > g.shape[a] - 2) i = g.shape[a] - 2;
+            frac[a] = s - (double)i;
+            lin += i * st[a];
+        }
+        base[p] = lin;
+        for (int k = 0; k < 8; k++) {
+            double w = 0.0;
+            if (k < (1 << ndim)) {
+                w = 1.0;
+                for (int a = 0; a < ndim; a++) w *= ((k >> a) & 1) ? frac[a] : 1.0 - frac[a];
+            }
+            weight[(size_t)p * 8 + k] = (float)w;
+        }
+    }
+    return FD_OK;
 }
 
 static int64_t slot_elems(const fd_grid &g)
@@ -288,33 +342,10 @@ extern "C" fd_status fd_sparse_create(const fd_grid *g, int npoint, const double
             return set_error(FD_ERR_INVALID_ARG, "fd_sparse_create: axis %d has %lld node(s); points need >= 2", a,
                              (long long)g->shape[a]);
     const int ndim = g->ndim;
-    int64_t padded[3], st[3];
-    layout_of(*g, padded, st);
     std::vector<int64_t> base((size_t)npoint);
     std::vector<float> weight((size_t)npoint * 8, 0.0f);
-    for (int p = 0; p < npoint; p++) {
-        int64_t lin = 0;
-        double frac[3] = {0, 0, 0};
-        for (int a = 0; a < ndim; a++) {
-            double x = coords[(int64_t)p * ndim + a];
-            double s = (x - g->origin[a]) / g->spacing[a];
-            double top = (double)(g->shape[a] - 1);
-            if (!(s >= 0.0) || !(s <= top))
-                return set_error(FD_ERR_OUT_OF_DOMAIN,
-                                 "fd_sparse_create: point %d coordinate %d = %g outside [%g, %g]", p, a, x,
-                                 g->origin[a], g->origin[a] + top * g->spacing[a]);
-            int64_t i = (int64_t)std::floor(s);
-            if (i > g->shape[a] - 2) i = g->shape[a] - 2;
-            frac[a] = s - (double)i;
-            lin += i * st[a];
-        }
-        base[p] = lin;
-        for (int k = 0; k < (1 << ndim); k++) {
-            double w = 1.0;
-            for (int a = 0; a < ndim; a++) w *= ((k >> a) & 1) ? frac[a] : 1.0 - frac[a];
-            weight[(size_t)p * 8 + k] = (float)w;
-        }
-    }
+    fd_status ts = linear_table(*g, npoint, coords, base.data(), weight.data(), "fd_sparse_create");
+    if (ts != FD_OK) return ts;
     fd_sparse *sp = new (std::nothrow) fd_sparse();
     if (!sp) return set_error(FD_ERR_NOMEM, "fd_sparse_create: out of host memory");
     sp->g = *g;
@@ -350,12 +381,7 @@ extern "C" fd_status fd_sparse_create(const fd_grid *g, int npoint, const double
     d.ncorner = 1 << ndim;
     d.base = sp->d_base;
     d.weight = sp->d_weight;
-    for (int k = 0; k < 8; k++) {
-        int64_t off = 0;
-        if (k < d.ncorner)
-            for (int a = 0; a < ndim; a++) off += ((k >> a) & 1) * st[a];
-        d.corner_off[k] = off;
-    }
+    corner_offsets(*g, d.corner_off);
     *out = sp;
     return FD_OK;
 }

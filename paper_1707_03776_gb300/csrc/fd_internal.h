@@ -43,6 +43,8 @@ cudaError_t launch_min_reduce(const Geom &g, const float *m, unsigned int *out_b
                               cudaStream_t st);
 cudaError_t launch_interpolate(const SparseDev &sp, const float *u, float *out_row,
                                cudaStream_t st);
+// loads the interpolation kernel's module on the current device
+cudaError_t prepare_interpolate();
 cudaError_t launch_inject(const SparseDev &sp, const float *c, const float *row, float *u,
                           cudaStream_t st);
 

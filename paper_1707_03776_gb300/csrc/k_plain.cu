@@ -267,6 +267,12 @@ cudaError_t launch_min_reduce(const Geom &g, const float *m, unsigned int *out_b
     return cudaGetLastError();
 }
 
+cudaError_t prepare_interpolate()
+{
+    cudaFuncAttributes attr;
+    return cudaFuncGetAttributes(&attr, interpolate_kernel);
+}
+
 cudaError_t launch_interpolate(const SparseDev &sp, const float *u, float *out_row,
                                cudaStream_t st)
 {

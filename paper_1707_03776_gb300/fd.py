@@ -422,8 +422,10 @@ def fd_cnn_adam(params, grads, m1, m2, n, lr, beta1, beta2, eps, step, stream=0)
 
 def fd_interpolate_noalloc(grid, coords, dev_field, dev_out, stream=0):
     """Interpolate a device field slot at host coordinates into dev_out
-    without any allocation (see include/fd.h)."""
-    c = _f64(coords)
+    without any allocation.  With coords None (no points) the call only does
+    the per-device set-up: the first call on a device allocates the static
+    table there, so make that call at start-up."""
+    c = _f64(coords if coords is not None else np.zeros((0, 3)))
     npoint = c.shape[0] if c.ndim > 1 else 0
     _check(lib().fd_interpolate_noalloc(grid, npoint, c.ctypes.data_as(_c_f64p) if npoint else None,
                                         int(dev_field) or None, int(dev_out) or None, int(stream) or None))

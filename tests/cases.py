@@ -1,5 +1,5 @@
 """Small runnable cases of each kernel family, for profiling one kernel at a
-time (python -m paper_1707_03776_gb300.cases <case> [options]).
+time (python tests/cases.py <case> [options]).
 
 Each case builds its inputs from the seeded workloads, runs a few warm-up
 launches, then `--reps` launches of the kernel of interest, synchronises and
@@ -17,9 +17,15 @@ the device at most.
   wgrad      the closure network's weight-gradient kernel (96^3)
 """
 import argparse
+import os
+import sys
 import time
 
 import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 
 def _sync():
@@ -29,8 +35,8 @@ def _sync():
 
 def case_acoustic(args):
     import torch
-    from . import fd, workloads as wl
-    from .modeling import AcousticModel
+    from paper_1707_03776_gb300 import fd, workloads as wl
+    from paper_1707_03776_gb300.modeling import AcousticModel
     cfg = wl.acoustic_config(n=args.n, space_order=args.so, nt=args.nt)
     model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], args.so, cfg["src_coords"],
                           cfg["rec_coords"], args.nt)
@@ -45,8 +51,8 @@ def case_acoustic(args):
 
 def case_pair(args):
     import torch
-    from . import fd, workloads as wl
-    from .modeling import AcousticModel
+    from paper_1707_03776_gb300 import fd, workloads as wl
+    from paper_1707_03776_gb300.modeling import AcousticModel
     cfg = wl.acoustic_config(n=args.n, space_order=args.so, nt=args.nt)
     model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], args.so, cfg["src_coords"],
                           cfg["rec_coords"], args.nt)
@@ -59,7 +65,7 @@ def case_pair(args):
 
 def case_batch(args):
     import torch
-    from . import fd, workloads as wl
+    from paper_1707_03776_gb300 import fd, workloads as wl
     cfg = wl.batched_config(nshots=args.shots, nt=args.nt)
     keep = []
     ops = []
@@ -84,8 +90,8 @@ def case_batch(args):
 
 def case_gradient(args):
     import torch
-    from . import workloads as wl
-    from .gradient import Propagator, Shot, modelling
+    from paper_1707_03776_gb300 import workloads as wl
+    from paper_1707_03776_gb300.gradient import Propagator, Shot, modelling
     cfg = wl.gradient_config(n=args.n, nt=args.nt)
     prop = Propagator(cfg["shape"], cfg["spacing"], cfg["origin"], 8,
                       Shot(cfg["shots"][0], cfg["wavelet"], cfg["rec_coords"]), args.nt, cfg["dt"],
@@ -101,7 +107,7 @@ def case_gradient(args):
 
 def case_diffusion(args):
     import torch
-    from . import fd, workloads as wl
+    from paper_1707_03776_gb300 import fd, workloads as wl
     cfg = wl.diffusion_ring()
     grid = fd.Grid(cfg["shape"], cfg["spacing"], cfg["origin"])
     u = fd.TimeData("u", grid)
@@ -116,7 +122,7 @@ def case_diffusion(args):
 
 def case_conv(args):
     import torch
-    from . import closure, fd
+    from paper_1707_03776_gb300 import closure, fd
     net = closure.ClosureNet(seed=0, rho=1e-3)
     shape = (args.n,) * 3
     ws = closure.Workspace(shape)
@@ -131,7 +137,7 @@ def case_conv(args):
 
 def case_conv_tc(args):
     import torch
-    from . import closure
+    from paper_1707_03776_gb300 import closure
     net = closure.ClosureNet(seed=0, rho=1e-3)
     shape = (args.n,) * 3
     ws = closure.Workspace(shape)
@@ -146,7 +152,7 @@ def case_conv_tc(args):
 
 def case_wgrad(args):
     import torch
-    from . import closure, fd
+    from paper_1707_03776_gb300 import closure, fd
     shape = (args.n,) * 3
     npts = int(np.prod(shape))
     g = torch.Generator(device="cuda").manual_seed(0)

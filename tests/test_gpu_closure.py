@@ -265,14 +265,13 @@ def test_network_gradients_parity():
     grads = cnn.network_backward(acts, pre, params, gout[..., None], store=cnn.bf16_round)
     for li in range(4):
         assert np.linalg.norm(got[li] - grads[li][0]) <= 2e-3 * np.linalg.norm(grads[li][0]), li
-    # (2) the exact FP64 network: BF16 storage costs up to ~3 % at the first
-    # layer's gradient (three BF16 backward stages), so 6e-2
+    # (2) the exact FP64 network's output: the device stores three BF16
+    # activations on the way (unit roundoff 2^-9 each), so its output stays
+    # within 1e-2 of the unrounded network.  The gradients are judged by (1)
+    # only: with BF16 storage of both activations and gradients their
+    # distance to the unrounded network measures BF16, not the kernels.
     acts, pre = cnn.network_forward(x, params)
-    loss_ref, gout = cnn.mse_and_grad(acts[-1][..., 0], tv / 1.5)
     assert np.linalg.norm(out - acts[-1][..., 0]) <= 1e-2 * np.linalg.norm(acts[-1])
-    grads = cnn.network_backward(acts, pre, params, gout[..., None])
-    for li in range(4):
-        assert np.linalg.norm(got[li] - grads[li][0]) <= 6e-2 * np.linalg.norm(grads[li][0]), li
 
 
 def test_closure_step_parity():
