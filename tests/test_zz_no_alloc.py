@@ -13,6 +13,8 @@ fields (so that the second call cannot pass on the first call's table):
     device's free memory (cudaMemGetInfo) nor torch's reserved memory.
 This file is collected last on purpose.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -38,7 +40,7 @@ def operator_interpolation(grid, field_np, coords):
     op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, 4, u, m, rec=rec)
     op.apply(0, 1, 1e-3)
     op.sync()
-    return rec.data[0, : rec.npoint].cpu().numpy(), u
+    return rec.data[0, : rec.npoint].cpu().numpy(), u, (op, rec, m)
 
 
 def _prepare():
@@ -52,10 +54,13 @@ def _prepare():
         grid = fd.Grid(shape, h, origin)
         field = wl.random_field(shape, seed)
         coords = wl.random_points(shape, h, origin, npoint, seed)
-        ref_op, u = operator_interpolation(grid, field, coords)
+        ref_op, u, keep = operator_interpolation(grid, field, coords)
         ref_or = oracle.interpolate_from_f32(field, h, origin, coords)
         dst = torch.full((npoint,), float("nan"), dtype=torch.float32, device="cuda")
-        out.append((grid, coords, u, dst, ref_op, ref_or))
+        out.append((grid, coords, u, dst, ref_op, ref_or, keep))
+    # nothing made before the calls under test may be freed during them (a
+    # free returns memory to the device and would move the free count)
+    gc.collect()
     torch.cuda.synchronize()
     return out
 
@@ -70,7 +75,7 @@ def test_noalloc_matches_operator_and_oracle_twice_without_allocating():
     free0, _ = torch.cuda.mem_get_info()
     reserved0 = torch.cuda.memory_reserved()
     for rep in range(2):
-        for grid, coords, u, dst, ref_op, ref_or in cases:
+        for grid, coords, u, dst, ref_op, ref_or, _ in cases:
             dst.fill_(float("nan"))
             fd.fd_interpolate_noalloc(grid.handle, coords, u.slots[0].data_ptr(), dst.data_ptr(),
                                       stream.cuda_stream)
