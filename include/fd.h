@@ -338,6 +338,22 @@ fd_status fd_operator_step(fd_operator *op, int64_t n, double dt, const void *u_
 fd_status fd_imaging_accumulate(const fd_grid *grid, double scale, const void *mu, const void *u0,
                                 const void *u1, const void *u2, void *grad, void *cuda_stream);
 
+/* Step n of the operator (as fd_operator_apply(op, n, 1, dt)) with the
+ * imaging condition above accumulated from the field the step writes:
+ * grad += scale * w * (u0 - 2 u1 + u2), w the new state (with
+ * FD_FLAG_REVERSE the adjoint state of time n, sources included).  This is
+ * the adjoint sweep and the imaging of the gradient in one pass over the
+ * grid (the paper's adjoint operator of the Seismic Inversion Example,
+ * extended to the gradient it serves): the tiled kernel accumulates the
+ * imaging as it writes w when it also injects the step's sources itself,
+ * else the imaging kernel runs after the step (the same arithmetic, bit for
+ * bit).  u0, u1, u2, grad: device FP32 slots in the layout of
+ * fd_field_layout, 32-byte aligned, none a slot of the operator's field.
+ * Errors: as fd_operator_apply, plus FD_ERR_LAYOUT for misaligned buffers
+ * and FD_ERR_UNSUPPORTED for non-acoustic operators. */
+fd_status fd_operator_apply_imaging(fd_operator *op, int64_t n, double dt, double scale, const void *u0,
+                                    const void *u1, const void *u2, void *grad);
+
 /* Tiling of the operator's tiled grid-update kernel (3D acoustic): tiles of
  * at most `rows` rows of d1 by 64 columns of d2, swept along d0, with
  * `stages` planes prefetched (2..4).  0 keeps the planner's choice for that

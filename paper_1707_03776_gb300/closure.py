@@ -16,8 +16,10 @@ normalises every sample by its own RMS and inference needs no scale.
 
 Layers: conv3x3x3(6 -> 16) ReLU, (16 -> 16) ReLU, (16 -> 16) ReLU, (16 -> 1);
 BF16 weights and activations, FP32 accumulation (libfdgb's fd_cnn_* tensor-
-core kernels); FP32 master weights updated by Adam.  Every step of training
-and inference runs in libfdgb's kernels; torch supplies device memory.
+core kernels: the mma.sync convolution by default, the tcgen05 one with its
+activations in tensor memory, identical results, as the alternative);
+FP32 master weights updated by Adam.  Every step of training and inference
+runs in libfdgb's kernels; torch supplies device memory.
 """
 import math
 
@@ -27,6 +29,9 @@ from . import fd
 
 CHANNELS = (6, 16, 16, 16, 1)
 NLAYER = len(CHANNELS) - 1
+# convolutions on the mma.sync kernel (fd_cnn_conv3d) unless a caller asks
+# for the tcgen05 one (fd_cnn_conv3d_tc); both give the same bits
+TENSOR_MEMORY = False
 
 
 def _stream():
@@ -65,10 +70,12 @@ class ClosureNet:
                      for i in range(NLAYER)]
         self.frag_t = [torch.zeros(_frag_bytes(CHANNELS[i]), dtype=torch.uint8, device="cuda")
                        for i in range(NLAYER)]
+        # tcgen05 operand layout of the same weights, forward and mirrored
+        self.frag_tc = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
+        self.frag_tc_t = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
+        self.tc_status = torch.zeros(1, dtype=torch.int32, device="cuda")
         self.rho = float(rho)
         self.vref = 3500.0
-        self.frag_tc = None  # tcgen05 operand layout, packed on first use
-        self.tc_status = None
         self.pack()
 
     def weight(self, li):
@@ -81,12 +88,21 @@ class ClosureNet:
 
     def pack(self):
         st = _stream()
-        self.frag_tc = None
         for li in range(NLAYER):
             cin, cout = CHANNELS[li], CHANNELS[li + 1]
             fd.fd_cnn_pack_weights(self.weight(li), cin, cout, 0, self.frag[li], st)
+            fd.fd_cnn_pack_weights_tc(self.weight(li), cin, cout, 0, self.frag_tc[li], st)
             if li > 0:
                 fd.fd_cnn_pack_weights(self.weight(li), cin, cout, 1, self.frag_t[li], st)
+                fd.fd_cnn_pack_weights_tc(self.weight(li), cin, cout, 1, self.frag_tc_t[li], st)
+
+    def check(self):
+        """Raise if a tcgen05 convolution gave up on a bounded wait (the
+        status word its kernels write; reading it synchronises)."""
+        code = int(self.tc_status.item())
+        if code != 0:
+            self.tc_status.zero_()
+            raise fd.FDError(code, "a tcgen05 convolution gave up on a bounded wait")
 
     def set_weights(self, ws):
         """Load FP32 weights [(27, cin, cout)] * NLAYER (numpy) and repack."""
@@ -119,17 +135,12 @@ class Workspace:
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
 
-def network_forward(net, ws, stream=None, tensor_memory=False):
-    """ws.h[0] (features) -> ws.out (FP32, one channel).  tensor_memory=True
-    runs the layers on the tcgen05 kernel instead (same results; slower with
-    16 channels, kept for comparison)."""
+def network_forward(net, ws, stream=None, tensor_memory=None):
+    """ws.h[0] (features) -> ws.out (FP32, one channel), on the tcgen05
+    kernel (tensor_memory True) or the mma.sync one (False; the default
+    TENSOR_MEMORY); the results are the same."""
     st = stream or _stream()
-    if tensor_memory and net.frag_tc is None:
-        import torch
-        net.frag_tc = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
-        net.tc_status = torch.zeros(1, dtype=torch.int32, device="cuda")
-        for li in range(NLAYER):
-            fd.fd_cnn_pack_weights_tc(net.weight(li), CHANNELS[li], CHANNELS[li + 1], 0, net.frag_tc[li], st)
+    tensor_memory = TENSOR_MEMORY if tensor_memory is None else tensor_memory
     for li in range(NLAYER):
         last = li == NLAYER - 1
         y = ws.out if last else ws.h[li + 1]
@@ -141,17 +152,22 @@ def network_forward(net, ws, stream=None, tensor_memory=False):
                              1 if last else 0, st)
 
 
-def network_backward(net, ws, stream=None):
+def network_backward(net, ws, stream=None, tensor_memory=None):
     """Accumulate net.grads from dL/dout in ws.g[0] (BF16, channel 0) through
     the activations of the last network_forward."""
     st = stream or _stream()
+    tensor_memory = TENSOR_MEMORY if tensor_memory is None else tensor_memory
     cur = 0
     for li in range(NLAYER - 1, -1, -1):
         cin, cout = CHANNELS[li], CHANNELS[li + 1]
         fd.fd_cnn_conv3d_wgrad(ws.shape, ws.h[li], ws.g[cur], cin, cout, net.grad(li), net.gb_dummy, st)
         if li > 0:
             # dL/dh_l = conv(g, flipped W_l) * (h_l > 0): h_l = relu(z_l)
-            fd.fd_cnn_conv3d(ws.shape, ws.g[cur], net.frag_t[li], None, cin, 0, ws.h[li], ws.g[1 - cur], 0, st)
+            if tensor_memory:
+                fd.fd_cnn_conv3d_tc(ws.shape, ws.g[cur], net.frag_tc_t[li], None, cin, 0, ws.h[li], ws.g[1 - cur], 0,
+                                    net.tc_status, st)
+            else:
+                fd.fd_cnn_conv3d(ws.shape, ws.g[cur], net.frag_t[li], None, cin, 0, ws.h[li], ws.g[1 - cur], 0, st)
             cur = 1 - cur
 
 

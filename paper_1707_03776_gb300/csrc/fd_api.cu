@@ -748,7 +748,11 @@ static cudaError_t interpolate_beside(fd_operator *op, const float *u, float *re
     return e;
 }
 
-extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt)
+// The time loop of fd_operator_apply; with `img`, every step also
+// accumulates the imaging condition from the field it writes -- fused into
+// the tiled kernel when that kernel fuses the step's sources too, else as a
+// separate kernel after the step (and its injection).
+static fd_status apply_steps(fd_operator *op, int64_t t0, int64_t nt, double dt, const ImagingArgs *img)
 {
     if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: null operator");
     if (nt < 0 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply: need t0 >= 0, nt >= 0");
@@ -815,6 +819,10 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                     FD_CUDA(launch_inject(op->src->dev, op->c, src_row, up, st), "inject");
                     op->launches += 1;
                 }
+                if (img) {
+                    FD_CUDA(launch_imaging(g, img->scale, up, img->u0, img->u1, img->u2, img->grad, st), "imaging");
+                    op->launches += 1;
+                }
             } else {
                 // receivers: a small kernel reading u^n, beside the update;
                 // sources: fused into the tiled kernel when the per-tile
@@ -826,14 +834,25 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
                         FD_CUDA(launch_interpolate(op->rec->dev, u, rec_row, st), "interpolate");
                     op->launches += 1;
                 }
+                // the imaging condition rides in the sweep when the value the
+                // sweep writes is final (sources fused or absent)
+                const bool fuse_img = img && (!src_row || op->tma.has_src);
                 FD_CUDA(profile_mark(op, 0), "profile");
-                FD_CUDA(launch_acoustic_tma(op->tma, M, g, op->coef, cur, op->status, src_row, st),
-                        "acoustic step");
+                if (fuse_img)
+                    FD_CUDA(launch_acoustic_tma_imaging(op->tma, M, op->coef, cur, op->status, src_row, *img, st),
+                            "acoustic step with imaging");
+                else
+                    FD_CUDA(launch_acoustic_tma(op->tma, M, g, op->coef, cur, op->status, src_row, st),
+                            "acoustic step");
                 FD_CUDA(profile_mark(op, 1), "profile");
                 op->launches += 1;
                 if (rec_row && beside) FD_CUDA(cudaStreamWaitEvent(st, op->ev_rec, 0), "interpolate");
                 if (src_row && !op->tma.has_src) {
                     FD_CUDA(launch_inject(op->src->dev, op->c, src_row, up, st), "inject");
+                    op->launches += 1;
+                }
+                if (img && !fuse_img) {
+                    FD_CUDA(launch_imaging(g, img->scale, up, img->u0, img->u1, img->u2, img->grad, st), "imaging");
                     op->launches += 1;
                 }
             }
@@ -872,6 +891,34 @@ extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, 
         }
     }
     return FD_OK;
+}
+
+extern "C" fd_status fd_operator_apply(fd_operator *op, int64_t t0, int64_t nt, double dt)
+{
+    return apply_steps(op, t0, nt, dt, nullptr);
+}
+
+extern "C" fd_status fd_operator_apply_imaging(fd_operator *op, int64_t n, double dt, double scale, const void *u0,
+                                               const void *u1, const void *u2, void *grad)
+{
+    if (!op) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply_imaging: null operator");
+    if (op->kind != FD_ACOUSTIC_LEAPFROG)
+        return set_error(FD_ERR_UNSUPPORTED, "fd_operator_apply_imaging: acoustic operators only");
+    if (!u0 || !u1 || !u2 || !grad) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply_imaging: null buffer");
+    for (const void *p : {u0, u1, u2, (const void *)grad})
+        if (((uintptr_t)p) % 32 != 0)
+            return set_error(FD_ERR_LAYOUT, "fd_operator_apply_imaging: buffer not 32-byte aligned");
+    for (const void *p : {u0, u1, u2, (const void *)grad})
+        if (p == op->u->slot[0] || p == op->u->slot[1])
+            return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply_imaging: a buffer is a slot of the operator's field");
+    if (!std::isfinite(scale)) return set_error(FD_ERR_INVALID_ARG, "fd_operator_apply_imaging: scale not finite");
+    ImagingArgs img;
+    img.u0 = (const float *)u0;
+    img.u1 = (const float *)u1;
+    img.u2 = (const float *)u2;
+    img.grad = (float *)grad;
+    img.scale = (float)scale;
+    return apply_steps(op, n, 1, dt, &img);
 }
 
 extern "C" fd_status fd_operator_sync(fd_operator *op)

@@ -36,6 +36,22 @@ struct SrcEntry {
     float w;
 };
 
+// The imaging condition of the adjoint-state gradient, fused into a step:
+// grad += scale * w * (u0 - 2 u1 + u2) at every point the step writes, w the
+// value it writes there (u0, u1, u2, grad in the slot layout).  Off when
+// grad is null.
+struct ImagingArgs {
+    const float *u0 = nullptr;
+    const float *u1 = nullptr;
+    const float *u2 = nullptr;
+    float *grad = nullptr;
+    float scale = 0.0f;
+};
+
+// The thread of a tiled sweep that owns an injected corner: its row and
+// group of 4 columns (the order of a plane's entries after the plane).
+__host__ __device__ inline int src_owner_key(const SrcEntry &e) { return e.r * (kTileW / 4) + (e.x >> 2); }
+
 // Device table of the fused source injection, sorted by (tile, plane), with
 // per-tile ranges.
 struct SparseFused {
@@ -106,6 +122,11 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
 // given and the plan fuses the sources.
 cudaError_t launch_acoustic_tma(const TmaPlan &plan, int M, const Geom &g, const Coef &cf,
                                 int cur, int *status, const float *src_row, cudaStream_t st);
+// The same step with the imaging condition fused (img.grad not null).  Only
+// valid when the step's sources are fused too (plan.has_src, or no sources):
+// the imaged value must be the final one.
+cudaError_t launch_acoustic_tma_imaging(const TmaPlan &plan, int M, const Coef &cf, int cur, int *status,
+                                        const float *src_row, const ImagingArgs &img, cudaStream_t st);
 
 // CTAs of the tiled kernel of half-width M and depth P resident per SM with
 // `threads` threads and `smem` bytes of dynamic shared memory (0 if none).

@@ -2,28 +2,31 @@
 // (tcgen05.mma with TMEM accumulators), the alternative to the mma.sync
 // kernel of k_cnn.cu with the same inputs, outputs and results.
 //
-// Implicit GEMM per output row of 128 points: D[128 points x 16 channels] =
-// sum over the 27 taps of A_tap[128 x 16] B_tap[16 x 16], one
-// tcgen05.mma.kind::f16 (M = 128, N = 16, K = 16, BF16 in, FP32 accumulate)
-// per tap, issued by one thread; the accumulators (2 rows x 16 columns, two
-// buffers by plane parity) live in tensor memory and are read back with
-// tcgen05.ld by the 4 warps (lane = point).  A CTA owns 2 rows x 128 points and
-// sweeps 16 planes along d0; each input plane (4 rows x 130 points with the
-// halo) arrives by two TMA copies of a 5D view of the activations (8 channels,
-// 2 halves, n2, n1, n0) -- zero outside the grid -- into a 5-plane ring, laid
-// out as the K-major no-swizzle core matrices of the A operand: channel half h
-// of plane point p at byte (h * points + p) * 16, so a tap's A tile is the
-// same layout started (p_tap * 16) bytes in (descriptor LBO = the half stride,
-// SBO = 128).  Weights: [27][2 halves][16 n][8 k] BF16 (LBO 256, SBO 128).
-// Plane loads, MMA completion (tcgen05.commit) and the epilogue are ordered by
-// mbarriers whose waits are bounded: a wait that gives up records
-// FD_ERR_TIMEOUT in the status word, drains what is still in flight and frees
-// the tensor memory before the CTA leaves.
-//
-// With only 16 output channels every MMA reads a 4 KB A tile for 65 kFLOP,
-// so the tensor core is bound by its shared-memory operand reads (measured:
-// tensor pipe 77 % busy at ~190 TFLOP/s), no faster per point than the
-// mma.sync kernel, which therefore remains the closure's path.
+// Implicit GEMM per output line of 128 points (the MMA's M = 128 TMEM lanes
+// along d2): D[128 x 16 channels] = sum over the 27 taps of A_tap[128 x 16]
+// B_tap[16 x 16], one tcgen05.mma.kind::f16 (M = 128, N = 16, K = 16, BF16 in,
+// FP32 accumulate) per tap.  With 16 output channels an MMA that takes its
+// 4 KB A tile from shared memory is bound by those reads (4 KB per 65 kFLOP),
+// so here the A operand lives in tensor memory:
+//   * a persistent CTA per SM (all 512 TMEM columns) sweeps tile columns of
+//     2 output rows x 128 points along d0; each input plane tile (4 rows x 130
+//     points x 16 channels, zero outside the grid) arrives by two TMA copies
+//     into a 6-plane shared-memory ring, laid out as K-major no-swizzle core
+//     matrices (channel half h of tile point p at byte (h * 520 + p) * 16);
+//   * tcgen05.cp copies each of its 4 input lines three times into a 4-plane
+//     TMEM ring, started 0, 1 and 2 points in: the three d2 shifts of the
+//     taps, so that lane i holds input point x0 + i - 1 + c for shift c;
+//   * the 54 MMAs of an output plane (2 rows x 27 taps) then read A from TMEM
+//     and only their 512-byte weight tile from shared memory, into one of two
+//     accumulator buffers (2 rows x 16 columns);
+//   * warps 0-3 read an accumulator buffer back with tcgen05.ld (lane =
+//     point), apply bias, ReLU and the input-gradient mask, store BF16 (or the
+//     one FP32 channel) and hand the buffer back; warp 4 issues everything.
+// TMA loads, cp and MMA completion (tcgen05.commit) and the epilogue are
+// ordered by mbarriers whose waits are bounded: a wait that gives up records
+// FD_ERR_TIMEOUT in the status word, the other role stops at its next wait,
+// and the CTA drains its copies and tensor-core work and frees the tensor
+// memory before it leaves.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -35,18 +38,28 @@ namespace fdgb {
 namespace {
 using namespace tile_dev;
 
-constexpr int kUC = 16;                   // channels per point
-constexpr int kUTR = 2;                   // output rows per CTA
-constexpr int kUW = 128;                  // output points per row = MMA M
-constexpr int kUPW = kUW + 2;             // plane row with the halo
-constexpr int kUPts = (kUTR + 2) * kUPW;  // points per plane
-constexpr int kURing = 5;                 // planes held
-constexpr int kUZc = 16;                  // planes per CTA
-constexpr int kUThreads = 128;            // 4 warps: TMEM lanes 0..127
-constexpr uint32_t kUTmemCols = 64;       // 2 accumulator buffers x kUTR x 16 columns
-constexpr uint32_t kPlaneBytes = kUPts * kUC * 2;
-constexpr uint32_t kWTapBytes = 512;      // [2 halves][16 n][8 k] BF16
-constexpr uint32_t kSmemU = kURing * kPlaneBytes + 27 * kWTapBytes + 8 * (kURing + 4);
+constexpr int kUC = 16;                               // channels per point
+constexpr int kTR = 2;                                // output rows per tile column
+constexpr int kTW = 128;                              // output points per line = MMA M = TMEM lanes
+constexpr int kPW = kTW + 2;                          // input line with the d2 halo
+constexpr int kInRows = kTR + 2;                      // input lines per plane tile
+constexpr int kPts = kInRows * kPW;                   // points per input plane tile
+constexpr uint32_t kHalfBytes = kPts * 16;            // one channel half of a tile (the A LBO)
+constexpr uint32_t kPlaneBytes = 2 * kHalfBytes;
+constexpr int kSRing = 6;                             // input planes in shared memory
+constexpr int kTRing = 4;                             // input planes in tensor memory
+constexpr uint32_t kPlaneCols = kInRows * 3 * 8;      // TMEM columns of an input plane (lines x shifts x K/2)
+constexpr uint32_t kAccCol = kTRing * kPlaneCols;     // first accumulator column
+constexpr uint32_t kTmemCols = 512;
+constexpr int kThreads = 160;                         // warps 0-3: epilogue; warp 4: copies and MMAs
+constexpr uint32_t kWTapBytes = 512;                  // [2 halves][16 n][8 k] BF16
+constexpr uint32_t kWOff = kSRing * kPlaneBytes;
+constexpr uint32_t kBarOff = kWOff + 27 * kWTapBytes;
+constexpr int kNBars = 2 * kSRing + 5;                // full, empty, mma_done[2], acc_free[2], fin
+constexpr uint32_t kSmemU = kBarOff + 8 * kNBars + 16;
+static_assert(kAccCol + 2 * kTR * 16 <= kTmemCols, "tensor memory layout");
+static_assert(kPlaneBytes % 128 == 0 && kHalfBytes % 128 == 0 && kWOff % 128 == 0, "TMA destinations");
+static_assert((kHalfBytes >> 4) < (1u << 14), "descriptor offset field");
 
 struct UDims {
     int n0, n1, n2;
@@ -66,19 +79,31 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 // instruction descriptor: D F32, A and B BF16, both K-major, N = 16, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+// D[tmem] (+)= A[tmem] * B[smem descriptor]
+__device__ __forceinline__ void umma_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+
+// 128 rows x 256 bits from shared memory (descriptor) into TMEM lanes 0..127
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc)
+{
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -95,39 +120,70 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Wait for phase `parity` of a barrier, giving up after kWaitLimitNs or as
+// soon as the CTA's abort flag is raised by the other role.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+// The work of a CTA: the linear range [q_lo, q_hi) of (tile column, output
+// plane) items, tile columns outermost; a segment is the run of it inside one
+// tile column.
+struct Seg {
+    int x0, y0, zs, ze;
+};
+
+__device__ __forceinline__ Seg segment_at(long long q, long long q_hi, const UDims &d, int tiles2)
+{
+    const long long col = q / d.n0;
+    const int zs = (int)(q - col * d.n0);
+    const long long end = min(q_hi, (col + 1) * (long long)d.n0);
+    Seg s;
+    s.x0 = (int)(col % tiles2) * kTW;
+    s.y0 = (int)(col / tiles2) * kTR;
+    s.zs = zs;
+    s.ze = zs + (int)(end - q);
+    return s;
+}
+
 template <bool RELU, bool MASK, bool OUT_F32>
-__global__ void __launch_bounds__(kUThreads, 2)
-    conv3d_umma_kernel(const __grid_constant__ CUtensorMap xmap, const uint4 *__restrict__ wpack,
+__global__ void __launch_bounds__(kThreads, 1)
+    conv3d_tmem_kernel(const __grid_constant__ CUtensorMap xmap, const uint4 *__restrict__ wpack,
                        const float *__restrict__ bias, int cout, const __nv_bfloat16 *__restrict__ mask, void *y,
                        UDims d, int *status)
 {
     extern __shared__ __align__(1024) unsigned char usm[];
     const uint32_t ring = smem_addr(usm);
-    const uint32_t wsm = ring + kURing * kPlaneBytes;
-    // barriers: full[kURing] (plane landed), done[2] (MMAs of a plane parity)
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(usm + kURing * kPlaneBytes + 27 * kWTapBytes);
-    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(bars + kURing + 2);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + kURing + 3);
-
-    const int tiles2 = (d.n2 + kUW - 1) / kUW;
-    const int col0 = (blockIdx.x % tiles2) * kUW;
-    const int row0 = (blockIdx.x / tiles2) * kUTR;
-    const int z0 = blockIdx.y * kUZc;
-    const int z1 = min(d.n0, z0 + kUZc);
+    const uint32_t wsm = ring + kWOff;
+    // barriers: full[kSRing] (plane landed), empty[kSRing] (its copies to
+    // TMEM done), mma_done[2] (an accumulator buffer's MMAs done),
+    // acc_free[2] (its epilogue done; 4 warp arrivals), fin (final drain)
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(usm + kBarOff);
+    constexpr int kFull = 0, kEmpty = kSRing, kDone = 2 * kSRing, kFree = 2 * kSRing + 2, kFin = 2 * kSRing + 4;
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(usm + kBarOff + 8 * kNBars);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(usm + kBarOff + 8 * kNBars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto BAR = [&](int i) { return smem_addr(&bars[i]); };
 
     for (int q = tid; q < 27 * (int)kWTapBytes / 16; q += blockDim.x)
-        reinterpret_cast<uint4 *>(usm + kURing * kPlaneBytes)[q] = wpack[q];
+        reinterpret_cast<uint4 *>(usm + kWOff)[q] = wpack[q];
     if (tid == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&xmap)) : "memory");
-        for (int i = 0; i < kURing + 2; i++) mbar_init(smem_addr(&bars[i]), 1);
+        for (int i = 0; i < kNBars; i++) mbar_init(BAR(i), (i == kFree || i == kFree + 1) ? 4u : 1u);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
-    if (warp == 0) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr((const void *)tmem_slot)),
-                     "r"(kUTmemCols));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     proxy_fence();  // the weights (generic stores) are read by the tensor core
@@ -136,169 +192,207 @@ __global__ void __launch_bounds__(kUThreads, 2)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // plane z -> ring slot z % kURing: both channel halves by TMA (zero outside)
-    unsigned loads_into[kURing];
-    for (int i = 0; i < kURing; i++) loads_into[i] = 0;
-    auto issue_plane = [&](int z) {
-        const int slot = ((z % kURing) + kURing) % kURing;
-        const uint32_t bar = smem_addr(&bars[slot]);
-        const uint32_t dst = ring + (uint32_t)slot * kPlaneBytes;
-        mbar_expect_tx(bar, kPlaneBytes);
-        for (int h = 0; h < 2; h++)
-            asm volatile(
-                "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst + (uint32_t)(h * kUPts * 16)),
-                "l"(reinterpret_cast<unsigned long long>(&xmap)), "r"(0), "r"(h), "r"(col0 - 1), "r"(row0 - 1),
-                "r"(z), "r"(bar)
-                : "memory");
-        loads_into[slot]++;
-    };
-    unsigned waited_full[kURing];
-    for (int i = 0; i < kURing; i++) waited_full[i] = 0;
-    auto wait_plane = [&](int z) {
-        const int slot = ((z % kURing) + kURing) % kURing;
-        const bool r = mbar_wait_bounded(smem_addr(&bars[slot]), waited_full[slot] & 1u);
-        if (r) waited_full[slot]++;  // a copy that did not land is still owed
-        return r;
-    };
-    if (tid == 0) {
-        issue_plane(z0 - 1);
-        issue_plane(z0);
-        issue_plane(z0 + 1);
-    }
+    const int tiles2 = (d.n2 + kTW - 1) / kTW;
+    const int tiles1 = (d.n1 + kTR - 1) / kTR;
+    const long long total = (long long)tiles2 * tiles1 * d.n0;
+    const long long q_lo = (long long)blockIdx.x * total / gridDim.x;
+    const long long q_hi = (long long)(blockIdx.x + 1) * total / gridDim.x;
 
-    unsigned waited[2] = {0u, 0u};
-    int issued_planes = 0;
-    bool ok = true;
-    // A descriptor offsets (16-byte units) of tap (b, c) and row r within a plane
-    const uint64_t lbo_sbo = ((uint64_t)((kUPts * 16u) >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);
-    const uint64_t bdesc0 = ((uint64_t)((wsm >> 4) & 0x3FFFu)) | ((uint64_t)(256u >> 4) << 16) |
-                            ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);
-
-    auto epilogue = [&](int p) {
-        const int b = p & 1;
-        const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&bars[kURing + b]), waited[b] & 1u));
-        if (!got) {
-            ok = false;
-            return;
-        }
-        waited[b]++;
-        tc_fence_after();
+    if (warp == 4) {
+        if (lane == 0) {
+            unsigned g_load = 0, g_full = 0;  // plane loads issued / whose arrival was waited (in order)
+            unsigned oq = 0;                  // output planes whose MMAs were issued
+            bool ok = true;
+            const uint64_t bdesc0 = umma_desc(wsm, 256, 128);
+            for (long long q = q_lo; q < q_hi && ok;) {
+                const Seg sg = segment_at(q, q_hi, d, tiles2);
+                const int nout = sg.ze - sg.zs, nin = nout + 2;
+                const unsigned load0 = g_load, oq0 = oq;
+                // input i of the segment is plane zs - 1 + i: shared slot
+                // (load0 + i) % kSRing, TMEM slot i % kTRing
+                auto load = [&](int i) -> bool {
+                    const unsigned g = load0 + (unsigned)i;
+                    const int slot = (int)(g % kSRing);
+                    // the slot's previous plane has been copied to TMEM
+                    if (g >= (unsigned)kSRing &&
+                        !mbar_wait_or_abort(BAR(kEmpty + slot), ((g / kSRing) - 1u) & 1u, abort_flag))
+                        return false;
+                    const uint32_t bar = BAR(kFull + slot);
+                    mbar_expect_tx(bar, kPlaneBytes);
+                    const uint32_t dst = ring + (uint32_t)slot * kPlaneBytes;
 #pragma unroll
-        for (int r = 0; r < kUTR; r++) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kUTR * 16 + r * 16), v);
-            const int gy = row0 + r, gx = col0 + 32 * warp + lane;
-            if (gy >= d.n1 || gx >= d.n2) continue;
-            const long long pt = ((long long)p * d.n1 + gy) * d.n2 + gx;
-            float f[16];
+                    for (int h = 0; h < 2; h++)
+                        asm volatile(
+                            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst + (uint32_t)h * kHalfBytes),
+                            "l"(reinterpret_cast<unsigned long long>(&xmap)), "r"(0), "r"(h), "r"(sg.x0 - 1),
+                            "r"(sg.y0 - 1), "r"(sg.zs - 1 + i), "r"(bar)
+                            : "memory");
+                    g_load++;
+                    return true;
+                };
+                auto cp_in = [&](int i) -> bool {
+                    const unsigned g = load0 + (unsigned)i;
+                    const int slot = (int)(g % kSRing);
+                    if (!mbar_wait_or_abort(BAR(kFull + slot), (g / kSRing) & 1u, abort_flag)) return false;
+                    g_full++;
+                    tc_fence_after();
+                    const uint32_t src = ring + (uint32_t)slot * kPlaneBytes;
+                    const uint32_t tcol = tmem + (uint32_t)(i % kTRing) * kPlaneCols;
 #pragma unroll
-            for (int o = 0; o < 16; o++) {
-                float t = __uint_as_float(v[o]) + ((bias && o < cout) ? bias[o] : 0.f);
-                if (RELU) t = fmaxf(t, 0.f);
-                f[o] = t;
-            }
-            if (MASK) {
-                const uint4 *mk = reinterpret_cast<const uint4 *>(mask + pt * kUC);
+                    for (int r = 0; r < kInRows; r++)
 #pragma unroll
-                for (int hh = 0; hh < 2; hh++) {
-                    const uint4 m4 = mk[hh];
-                    const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+                        for (int c = 0; c < 3; c++)
+                            tmem_cp_128x256b(tcol + (uint32_t)((r * 3 + c) * 8),
+                                             umma_desc(src + (uint32_t)((r * kPW + c) * 16), kHalfBytes, 128));
+                    umma_commit(BAR(kEmpty + slot));
+                    return true;
+                };
+                const int npre = nin < kSRing ? nin : kSRing;
+                for (int i = 0; i < npre && ok; i++) ok = load(i);
+                for (int i = 0; i < 3 && ok; i++) ok = cp_in(i);
+                int next_load = npre, next_cp = 3;
+                for (int o = 0; o < nout && ok; o++) {
+                    const unsigned b = oq & 1u;
+                    // the epilogue has read this accumulator buffer back
+                    if (oq >= 2 && !mbar_wait_or_abort(BAR(kFree + b), ((oq >> 1) - 1u) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dcol = tmem + kAccCol + b * 32u;
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw[j]);
-                        if (!(__low2float(m2) > 0.f)) f[hh * 8 + 2 * j] = 0.f;
-                        if (!(__high2float(m2) > 0.f)) f[hh * 8 + 2 * j + 1] = 0.f;
+                    for (int a = 0; a < 3; a++) {
+                        const uint32_t pl = tmem + (uint32_t)((o + a) % kTRing) * kPlaneCols;
+#pragma unroll
+                        for (int bb = 0; bb < 3; bb++)
+#pragma unroll
+                            for (int c = 0; c < 3; c++) {
+                                const int t = a * 9 + bb * 3 + c;
+#pragma unroll
+                                for (int ro = 0; ro < kTR; ro++)
+                                    umma_tmem_a(dcol + (uint32_t)(ro * 16), pl + (uint32_t)(((ro + bb) * 3 + c) * 8),
+                                                bdesc0 + (uint64_t)(t * (kWTapBytes >> 4)), t > 0 ? 1u : 0u);
+                            }
+                    }
+                    umma_commit(BAR(kDone + b));
+                    oq++;
+                    if (next_cp < nin) {
+                        // the TMEM slot of input next_cp - kTRing is free
+                        // once the last output reading it (that index) is done
+                        if (next_cp >= kTRing) {
+                            const unsigned ow = oq0 + (unsigned)(next_cp - kTRing);
+                            if (!mbar_wait_or_abort(BAR(kDone + (ow & 1u)), (ow >> 1) & 1u, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (!cp_in(next_cp++)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (next_load < nin && !load(next_load++)) {
+                        ok = false;
+                        break;
                     }
                 }
-            }
-            if (OUT_F32) {
-                reinterpret_cast<float *>(y)[pt] = f[0];
-            } else {
-                uint32_t packed[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const __nv_bfloat162 t2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-                    packed[j] = *reinterpret_cast<const uint32_t *>(&t2);
+                // the segment's last commit covers every copy and MMA of it:
+                // afterwards all TMEM and shared slots are free
+                if (ok && oq > oq0) {
+                    const unsigned ow = oq - 1;
+                    ok = mbar_wait_or_abort(BAR(kDone + (ow & 1u)), (ow >> 1) & 1u, abort_flag);
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(y) + pt * kUC);
-                dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                q += nout;
             }
-        }
-        tc_fence_before();
-    };
-
-    for (int z = z0; z < z1; z++) {
-        // every warp is done with the TMEM buffer the MMAs below overwrite
-        // (its epilogue ran two planes ago) and with nothing else
-        __syncthreads();
-        if (*abort_flag) break;
-        if (tid == 0) {
-            // plane z+2 goes where plane z-3 was: its last readers (the MMAs
-            // of plane z-2) finished before the epilogue of z-2
-            issue_plane(z + 2);
-            bool good = true;
-            if (z == z0) good = wait_plane(z - 1) && wait_plane(z);
-            good = good && wait_plane(z + 1);
-            if (!good) {
+            if (!ok) {
                 *abort_flag = 1;
-            } else {
+                atomicExch(status, (int)FD_ERR_TIMEOUT);
+            }
+            // drain: plane copies still owed, then every tcgen05 operation
+            // issued (one more commit), under one shared deadline
+            const unsigned long long deadline = global_ns() + kWaitLimitNs;
+            for (unsigned g = g_full; g < g_load; g++)
+                mbar_wait_until(BAR(kFull + (int)(g % kSRing)), (g / kSRing) & 1u, deadline);
+            umma_commit(BAR(kFin));
+            mbar_wait_until(BAR(kFin), 0u, deadline);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 = points x0+32w..
+        unsigned oq = 0;
+        bool ok = true;
+        for (long long q = q_lo; q < q_hi && ok;) {
+            const Seg sg = segment_at(q, q_hi, d, tiles2);
+            for (int z = sg.zs; z < sg.ze; z++) {
+                const unsigned b = oq & 1u;
+                const bool got =
+                    __all_sync(0xffffffffu, mbar_wait_or_abort(BAR(kDone + b), (oq >> 1) & 1u, abort_flag));
+                if (!got) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)((z & 1) * kUTR * 16);
-                uint64_t adesc_plane[3];
 #pragma unroll
-                for (int a = 0; a < 3; a++)
-                    adesc_plane[a] = lbo_sbo |
-                                     (uint64_t)(((ring + (uint32_t)((z - 1 + a + kURing) % kURing) * kPlaneBytes) >> 4) &
-                                                0x3FFFu);
+                for (int ro = 0; ro < kTR; ro++) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + kAccCol + b * 32u + (uint32_t)(ro * 16), v);
+                    const int gy = sg.y0 + ro, gx = sg.x0 + 32 * warp + lane;
+                    if (gy >= d.n1 || gx >= d.n2) continue;
+                    const long long pt = ((long long)z * d.n1 + gy) * d.n2 + gx;
+                    float f[16];
 #pragma unroll
-                for (int t = 0; t < 27; t++) {
-                    const int a = t / 9, bb = (t / 3) % 3 - 1, c = t % 3 - 1;
-                    const uint64_t bdesc = bdesc0 + (uint64_t)(t * (kWTapBytes >> 4));
+                    for (int o = 0; o < 16; o++) {
+                        float t = __uint_as_float(v[o]) + ((bias && o < cout) ? bias[o] : 0.f);
+                        if (RELU) t = fmaxf(t, 0.f);
+                        f[o] = t;
+                    }
+                    if (MASK) {
+                        const uint4 *mk = reinterpret_cast<const uint4 *>(mask + pt * kUC);
 #pragma unroll
-                    for (int r = 0; r < kUTR; r++) {
-                        const uint32_t off = (uint32_t)((r + 1 + bb) * kUPW + 1 + c);  // points = 16-byte units
-                        umma_bf16(acc + (uint32_t)(r * 16), adesc_plane[a] + off, bdesc, t > 0 ? 1u : 0u);
+                        for (int hh = 0; hh < 2; hh++) {
+                            const uint4 m4 = mk[hh];
+                            const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw[j]);
+                                if (!(__low2float(m2) > 0.f)) f[hh * 8 + 2 * j] = 0.f;
+                                if (!(__high2float(m2) > 0.f)) f[hh * 8 + 2 * j + 1] = 0.f;
+                            }
+                        }
+                    }
+                    if (OUT_F32) {
+                        reinterpret_cast<float *>(y)[pt] = f[0];
+                    } else {
+                        uint32_t packed[8];
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const __nv_bfloat162 t2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+                            packed[j] = *reinterpret_cast<const uint32_t *>(&t2);
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(y) + pt * kUC);
+                        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                     }
                 }
-                umma_commit(smem_addr(&bars[kURing + (z & 1)]));
+                // this buffer's values are in registers: hand it back
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(BAR(kFree + b));
+                oq++;
             }
+            q += sg.ze - sg.zs;
         }
-        __syncthreads();
-        if (*abort_flag) break;
-        issued_planes++;
-        if (z > z0) epilogue(z - 1);
-        if (!ok) *abort_flag = 1;
-    }
-    if (ok && !*abort_flag && z1 > z0) epilogue(z1 - 1);
-    // after a wait gave up, every barrier still owed is waited on under one
-    // shared deadline, so one that never completes does not stop the drain
-    // short of the others
-    const bool aborted = !ok || *abort_flag;
-    const unsigned long long deadline = global_ns() + kWaitLimitNs;
-    if (aborted) {
-        if (tid == 0) atomicExch(status, (int)FD_ERR_TIMEOUT);
-        for (int b = 0; b < 2; b++) {
-            const unsigned owed = (unsigned)((issued_planes + (b == 0 ? 1 : 0)) / 2);
-            while (waited[b] < owed) {
-                if (!mbar_wait_until(smem_addr(&bars[kURing + b]), waited[b] & 1u, deadline)) break;
-                waited[b]++;
-            }
+        if (!ok && lane == 0) {
+            *abort_flag = 1;
+            atomicExch(status, (int)FD_ERR_TIMEOUT);
         }
     }
-    // the TMA copies still owed (planes issued but never consumed)
-    if (tid == 0)
-        for (int i = 0; i < kURing; i++)
-            while (waited_full[i] < loads_into[i]) {
-                if (!mbar_wait_until(smem_addr(&bars[i]), waited_full[i] & 1u, deadline)) break;
-                waited_full[i]++;
-            }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 4) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
 
@@ -374,7 +468,7 @@ extern "C" fd_status fd_cnn_conv3d_tc(const int64_t *shape, const void *x, const
     CUtensorMap map;
     cuuint64_t dims[5] = {8, 2, (cuuint64_t)d.n2, (cuuint64_t)d.n1, (cuuint64_t)d.n0};
     cuuint64_t strides[4] = {16, 32, 32ull * d.n2, 32ull * d.n2 * d.n1};
-    cuuint32_t box[5] = {8, 1, (cuuint32_t)kUPW, (cuuint32_t)(kUTR + 2), 1};
+    cuuint32_t box[5] = {8, 1, (cuuint32_t)kPW, (cuuint32_t)kInRows, 1};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     EncodeFn enc = get_encode();
     if (!enc) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -382,17 +476,27 @@ extern "C" fd_status fd_cnn_conv3d_tc(const int64_t *shape, const void *x, const
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return set_error(FD_ERR_CUDA, "fd_cnn_conv3d_tc: tensor map encoding failed");
-    dim3 grid((unsigned)(((d.n2 + kUW - 1) / kUW) * ((d.n1 + kUTR - 1) / kUTR)), (unsigned)((d.n0 + kUZc - 1) / kUZc));
+    // persistent: one CTA per SM (each holds all of its SM's tensor memory),
+    // each taking an equal share of the (tile column, plane) items
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            return set_error(FD_ERR_CUDA, "fd_cnn_conv3d_tc: device query failed");
+    }
+    const long long items = (long long)((d.n2 + kTW - 1) / kTW) * ((d.n1 + kTR - 1) / kTR) * d.n0;
+    dim3 grid((unsigned)(items < sms ? items : sms));
     cudaStream_t st = (cudaStream_t)stream;
     const __nv_bfloat16 *mk = (const __nv_bfloat16 *)mask;
     const uint4 *wp = (const uint4 *)wpack;
     cudaError_t e = cudaSuccess;
 #define LAUNCH(R, M, F)                                                                                   \
     do {                                                                                                  \
-        auto k = conv3d_umma_kernel<R, M, F>;                                                             \
+        auto k = conv3d_tmem_kernel<R, M, F>;                                                             \
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemU);            \
         if (e == cudaSuccess) {                                                                           \
-            k<<<grid, kUThreads, kSmemU, st>>>(map, wp, bias, cout, mk, y, d, status);                    \
+            k<<<grid, kThreads, kSmemU, st>>>(map, wp, bias, cout, mk, y, d, status);                     \
             e = cudaGetLastError();                                                                       \
         }                                                                                                 \
     } while (0)

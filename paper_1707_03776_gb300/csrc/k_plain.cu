@@ -150,14 +150,16 @@ __global__ void imaging_kernel(Geom g, float scale, const float *__restrict__ mu
             const float4 b = *reinterpret_cast<const float4 *>(u1 + at);
             const float4 e = *reinterpret_cast<const float4 *>(u2 + at);
             float4 gr = *reinterpret_cast<const float4 *>(grad + at);
-            gr.x = fmaf(scale * m4.x, a.x - 2.0f * b.x + e.x, gr.x);
-            gr.y = fmaf(scale * m4.y, a.y - 2.0f * b.y + e.y, gr.y);
-            gr.z = fmaf(scale * m4.z, a.z - 2.0f * b.z + e.z, gr.z);
-            gr.w = fmaf(scale * m4.w, a.w - 2.0f * b.w + e.w, gr.w);
+            // explicit FMAs, the order of the imaging fused into the tiled
+            // adjoint step, so that the two agree bit for bit
+            gr.x = fmaf(scale * m4.x, fmaf(-2.0f, b.x, a.x) + e.x, gr.x);
+            gr.y = fmaf(scale * m4.y, fmaf(-2.0f, b.y, a.y) + e.y, gr.y);
+            gr.z = fmaf(scale * m4.z, fmaf(-2.0f, b.z, a.z) + e.z, gr.z);
+            gr.w = fmaf(scale * m4.w, fmaf(-2.0f, b.w, a.w) + e.w, gr.w);
             *reinterpret_cast<float4 *>(grad + at) = gr;
         } else {
             for (int64_t k = 0; c0 + k < g.n[2]; k++)
-                grad[at + k] = fmaf(scale * mu[at + k], u0[at + k] - 2.0f * u1[at + k] + u2[at + k], grad[at + k]);
+                grad[at + k] = fmaf(scale * mu[at + k], fmaf(-2.0f, u1[at + k], u0[at + k]) + u2[at + k], grad[at + k]);
         }
     }
 }

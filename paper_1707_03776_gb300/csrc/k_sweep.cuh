@@ -200,12 +200,14 @@ __device__ inline void init_barriers(const SweepSmem &sm)
 // output plane reads).  it_u / it_a count the u^n and aux loads this CTA has
 // consumed so far (ring slots and barrier phases continue across columns).
 // Returns false when a wait gave up (status set, copies drained).
-template <int M, int P>
+// With IMG, the imaging condition of `img` is accumulated at every point
+// written, from the value written (sources included).
+template <int M, int P, bool IMG = false>
 __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
                              const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
                              int tile, int z_lo, int z_hi, const SrcEntry *__restrict__ src_tab, int nsrc,
                              const float *__restrict__ src_row, const SweepSmem &sm, unsigned &it_u, unsigned &it_a,
-                             int *status)
+                             int *status, const ImagingArgs &img = ImagingArgs())
 {
     constexpr int NU = M + 1 + P;     // u^n planes alive: M behind the newest, the newest, P in flight
     constexpr int NA = P + 1;         // aux planes (u^{n-1}, c, d)
@@ -291,6 +293,38 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
 #pragma unroll
     for (int k = 0; k < Q; k++) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
 
+    // imaging inputs (u0, u1, u2, grad) of the next output plane, loaded one
+    // iteration ahead into registers (up to M = 6; the highest orders load
+    // them when used), after an L2 prefetch three iterations ahead, so that
+    // their DRAM latency overlaps planes of work
+    constexpr bool kImgRegs = IMG && M <= 6;
+    float4 img_cur[4], img_next[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) img_cur[k] = img_next[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto img_fetch = [&](int zo_f, float4 (&dst)[4]) {
+        const long long at = (long long)zo_f * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
+        const float *src[4] = {img.u0, img.u1, img.u2, img.grad};
+        if (col0 + 4 * qc + 3 < a.n2) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) dst[k] = *reinterpret_cast<const float4 *>(src[k] + at);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if (col0 + 4 * qc + i < a.n2) v[i] = src[k][at + i];
+                dst[k] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    };
+    auto img_prefetch_l2 = [&](int zo_f) {
+        const long long at = (long long)zo_f * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
+        const float *src[4] = {img.u0, img.u1, img.u2, img.grad};
+#pragma unroll
+        for (int k = 0; k < 4; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(src[k] + at));
+    };
+
     int j = 0;
     bool ok = true, stop = false;
     // at high orders the d0 queue shift (2M+1 float4 moves per plane) is a
@@ -299,6 +333,13 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
 #pragma unroll(M >= 6 ? 2 : 1)
     for (; j < J; j++) {
         if (tid == 0 && j + P < J) issue(j + P);
+        if constexpr (IMG) {
+            // output plane of the next iteration into registers, and the one
+            // two further into L2 (so that the register loads find it there)
+            const int zn = z_lo + j + 1 - 2 * M;
+            if (active && zn + 2 >= z_lo && zn + 2 < z_hi) img_prefetch_l2(zn + 2);
+            if (kImgRegs && active && zn >= z_lo && zn < z_hi) img_fetch(zn, img_next);
+        }
         ok = wait_u(j) && ok;
 #pragma unroll
         for (int k = 0; k < Q - 1; k++) q[k] = q[k + 1];
@@ -375,33 +416,69 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
                 }
                 if (nsrc > 0) {
                     // source injection at the corners this thread owns on plane ja
+                    // (a plane's entries are sorted by owning thread: binary
+                    // search for this thread's first, then its run)
                     float inj0 = 0.f, inj1 = 0.f, inj2 = 0.f, inj3 = 0.f;
                     const int s_end = s_sstart[zo + 1];
-                    for (int k = s_sstart[zo]; k < s_end; k++) {
+                    const int key = r * (kTileW / 4) + qc;
+                    int lo = s_sstart[zo], hi = s_end;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (src_owner_key(s_src[mid]) < key) lo = mid + 1; else hi = mid;
+                    }
+                    for (int k = lo; k < s_end; k++) {
                         const SrcEntry e = s_src[k];
-                        if (e.r == r && (e.x >> 2) == qc) {
-                            const float sv = e.w * src_row[e.p];
-                            const int i = e.x & 3;
-                            inj0 += (i == 0) ? sv : 0.f;
-                            inj1 += (i == 1) ? sv : 0.f;
-                            inj2 += (i == 2) ? sv : 0.f;
-                            inj3 += (i == 3) ? sv : 0.f;
-                        }
+                        if (src_owner_key(e) != key) break;
+                        const float sv = e.w * src_row[e.p];
+                        const int i = e.x & 3;
+                        inj0 += (i == 0) ? sv : 0.f;
+                        inj1 += (i == 1) ? sv : 0.f;
+                        inj2 += (i == 2) ? sv : 0.f;
+                        inj3 += (i == 3) ? sv : 0.f;
                     }
                     res[0] = fmaf(inj0, cv[0], res[0]);
                     res[1] = fmaf(inj1, cv[1], res[1]);
                     res[2] = fmaf(inj2, cv[2], res[2]);
                     res[3] = fmaf(inj3, cv[3], res[3]);
                 }
-                float *o = out + (long long)zo * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
-                if (col0 + 4 * qc + 3 < a.n2) {
+                const long long at = (long long)zo * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
+                float *o = out + at;
+                const bool full = col0 + 4 * qc + 3 < a.n2;
+                if (full) {
                     *reinterpret_cast<float4 *>(o) = make_float4(res[0], res[1], res[2], res[3]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 4; i++)
                         if (col0 + 4 * qc + i < a.n2) o[i] = res[i];
                 }
+                if constexpr (IMG) {
+                    // grad += scale * w * (u0 - 2 u1 + u2), the same two FMAs
+                    // and add as the separate imaging kernel
+                    if (!kImgRegs) img_fetch(zo, img_cur);
+                    if (full) {
+                        const float4 x0 = img_cur[0], x1 = img_cur[1], x2 = img_cur[2];
+                        float4 gr = img_cur[3];
+                        gr.x = fmaf(img.scale * res[0], fmaf(-2.0f, x1.x, x0.x) + x2.x, gr.x);
+                        gr.y = fmaf(img.scale * res[1], fmaf(-2.0f, x1.y, x0.y) + x2.y, gr.y);
+                        gr.z = fmaf(img.scale * res[2], fmaf(-2.0f, x1.z, x0.z) + x2.z, gr.z);
+                        gr.w = fmaf(img.scale * res[3], fmaf(-2.0f, x1.w, x0.w) + x2.w, gr.w);
+                        *reinterpret_cast<float4 *>(img.grad + at) = gr;
+                    } else {
+                        const float x0[4] = {img_cur[0].x, img_cur[0].y, img_cur[0].z, img_cur[0].w};
+                        const float x1[4] = {img_cur[1].x, img_cur[1].y, img_cur[1].z, img_cur[1].w};
+                        const float x2[4] = {img_cur[2].x, img_cur[2].y, img_cur[2].z, img_cur[2].w};
+                        const float gr[4] = {img_cur[3].x, img_cur[3].y, img_cur[3].z, img_cur[3].w};
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            if (col0 + 4 * qc + i < a.n2)
+                                img.grad[at + i] = fmaf(img.scale * res[i], fmaf(-2.0f, x1[i], x0[i]) + x2[i], gr[i]);
+                    }
+                }
             }
+        }
+        if constexpr (kImgRegs) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) img_cur[k] = img_next[k];
         }
         if (!ok) *sm.abort = 1;
         __syncthreads();

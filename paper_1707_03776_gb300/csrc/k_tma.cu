@@ -36,13 +36,13 @@ namespace {
 
 using namespace tile_dev;
 
-template <int M, int P>
+template <int M, int P, bool IMG>
 __global__ void __launch_bounds__(16 * kMaxRows, 1)
     acoustic_tma_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_um,
                         const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_d,
                         float *__restrict__ out, const TileArgs a, const Coef cf, int *status,
                         const SrcEntry *__restrict__ src_tab, const int *__restrict__ src_off,
-                        const float *__restrict__ src_row, const int src_cap)
+                        const float *__restrict__ src_row, const int src_cap, const ImagingArgs img)
 {
     // an earlier launch of this operator gave up on a wait: do nothing until
     // the host has read and cleared the status word
@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
         return;
     }
     unsigned it_u = 0, it_a = 0;
-    sweep_column<M, P>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc, src_row,
-                       sm, it_u, it_a, status);
+    sweep_column<M, P, IMG>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc,
+                            src_row, sm, it_u, it_a, status, img);
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -122,12 +122,16 @@ constexpr size_t kSparseReserve = 16 * 1024;  // shared memory kept for fused po
 template <int M>
 cudaError_t configure_kernel(size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(acoustic_tma_kernel<M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(acoustic_tma_kernel<M, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(acoustic_tma_kernel<M, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto kernel) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    };
+    set(acoustic_tma_kernel<M, 2, false>);
+    set(acoustic_tma_kernel<M, 3, false>);
+    set(acoustic_tma_kernel<M, 4, false>);
+    set(acoustic_tma_kernel<M, 2, true>);
+    set(acoustic_tma_kernel<M, 3, true>);
+    set(acoustic_tma_kernel<M, 4, true>);
     return e;
 }
 
@@ -342,7 +346,12 @@ void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vecto
         }
     }
     for (int t = 0; t < tiles; t++) {
-        std::stable_sort(per[t].begin(), per[t].end(), [](const SrcEntry &x, const SrcEntry &y) { return x.z < y.z; });
+        // by plane, then by the thread owning the corner (row, 4-column
+        // group): a thread finds its entries by binary search; stable, so the
+        // entries of one point stay in (point, corner) order
+        std::stable_sort(per[t].begin(), per[t].end(), [](const SrcEntry &x, const SrcEntry &y) {
+            return x.z != y.z ? x.z < y.z : src_owner_key(x) < src_owner_key(y);
+        });
         off[t] = (int)all.size();
         all.insert(all.end(), per[t].begin(), per[t].end());
         max_per_tile = std::max(max_per_tile, (int)per[t].size());
@@ -427,7 +436,8 @@ int tma_occupancy(int M, int P, int threads, size_t smem)
     switch (M * 8 + P) {
 #define CASE(MM, PP)                                                                                      \
     case MM * 8 + PP:                                                                                     \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, acoustic_tma_kernel<MM, PP>, threads, smem); \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, acoustic_tma_kernel<MM, PP, false>, threads, \
+                                                          smem);                                          \
         break;
 #define CASES(MM) CASE(MM, 2) CASE(MM, 3) CASE(MM, 4)
         CASES(1) CASES(2) CASES(3) CASES(4) CASES(5) CASES(6) CASES(7) CASES(8)
@@ -439,18 +449,24 @@ int tma_occupancy(int M, int P, int threads, size_t smem)
 
 static cudaError_t launch_maps(const TmaPlan &plan, int M, const Coef &cf, const CUtensorMap &map_cur,
                                const CUtensorMap &map_prev, float *out, int *status, const float *src_row,
-                               cudaStream_t st)
+                               cudaStream_t st, const ImagingArgs &img = ImagingArgs())
 {
     dim3 grid((unsigned)(plan.args.k1 * plan.args.k2 * plan.args.kz));
     dim3 block((unsigned)plan.threads);
     const float *srow = plan.has_src ? src_row : nullptr;
     const int key = M * 8 + plan.stages;
+    const bool image = img.grad != nullptr;
     switch (key) {
 #define CASE(MM, PP)                                                                                      \
     case MM * 8 + PP:                                                                                     \
-        acoustic_tma_kernel<MM, PP><<<grid, block, plan.smem, st>>>(                                      \
-            map_cur, map_prev, plan.c_tile, plan.d_tile, out, plan.args, cf, status, plan.fused.src,      \
-            plan.fused.src_off, srow, plan.src_cap);                                                      \
+        if (image)                                                                                        \
+            acoustic_tma_kernel<MM, PP, true><<<grid, block, plan.smem, st>>>(                            \
+                map_cur, map_prev, plan.c_tile, plan.d_tile, out, plan.args, cf, status, plan.fused.src,  \
+                plan.fused.src_off, srow, plan.src_cap, img);                                             \
+        else                                                                                              \
+            acoustic_tma_kernel<MM, PP, false><<<grid, block, plan.smem, st>>>(                           \
+                map_cur, map_prev, plan.c_tile, plan.d_tile, out, plan.args, cf, status, plan.fused.src,  \
+                plan.fused.src_off, srow, plan.src_cap, img);                                             \
         break;
 #define CASES(MM) CASE(MM, 2) CASE(MM, 3) CASE(MM, 4)
         CASES(1) CASES(2) CASES(3) CASES(4) CASES(5) CASES(6) CASES(7) CASES(8)
@@ -468,6 +484,13 @@ cudaError_t launch_acoustic_tma(const TmaPlan &plan, int M, const Geom &g, const
     (void)g;
     const int prev = cur ^ 1;
     return launch_maps(plan, M, cf, plan.u_halo[cur], plan.u_tile[prev], plan.slot[prev], status, src_row, st);
+}
+
+cudaError_t launch_acoustic_tma_imaging(const TmaPlan &plan, int M, const Coef &cf, int cur, int *status,
+                                        const float *src_row, const ImagingArgs &img, cudaStream_t st)
+{
+    const int prev = cur ^ 1;
+    return launch_maps(plan, M, cf, plan.u_halo[cur], plan.u_tile[prev], plan.slot[prev], status, src_row, st, img);
 }
 
 static const CUtensorMap *cached_map(TmaPlan &plan, const float *ptr, bool halo)

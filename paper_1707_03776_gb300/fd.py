@@ -79,6 +79,8 @@ _SIGNATURES = [
     ("fd_interpolate_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _c_f64p, _vp, _vp, _vp]),
     ("fd_operator_step", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp]),
     ("fd_imaging_accumulate", ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fd_operator_apply_imaging", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _vp, _vp,
+                                                 _vp, _vp]),
     ("fd_operator_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     ("fd_operator_autotune", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _c_f64p]),
@@ -290,6 +292,13 @@ def fd_imaging_accumulate(grid, scale, mu, u0, u1, u2, grad, stream=0):
     """grad += scale * mu * (u0 - 2 u1 + u2) (device pointers)."""
     _check(lib().fd_imaging_accumulate(grid, float(scale), int(mu), int(u0), int(u1), int(u2), int(grad),
                                        int(stream) or None))
+
+
+def fd_operator_apply_imaging(op, n, dt, scale, u0, u1, u2, grad):
+    """Step n of the operator with grad += scale * w * (u0 - 2 u1 + u2)
+    accumulated from the field w the step writes (device pointers)."""
+    _check(lib().fd_operator_apply_imaging(op, int(n), float(dt), float(scale), int(u0), int(u1), int(u2),
+                                           int(grad)))
 
 
 def fd_operator_set_tiling(op, rows=0, stages=0):

@@ -11,7 +11,8 @@ segments from last to first; inside each segment the forward states are
 recomputed from its checkpoint with out-of-place steps (fd_operator_step) into
 a segment buffer, and the imaging condition
     dJ/dm += -(1/dt^2) mu^n (u^n - 2u^{n-1} + u^{n-2})
-is accumulated by fd_imaging_accumulate after every adjoint step.
+is accumulated in the same pass as every adjoint step
+(fd_operator_apply_imaging: fused into the tiled sweep).
 
 Every step of the path runs in libfdgb's kernels; torch provides the device
 memory (fields, checkpoints, the segment buffer) and the autograd plumbing.
@@ -131,17 +132,16 @@ class Propagator:
         for s in self.mu.slots:
             s.zero_()
         self.grad.slots[0].zero_()
-        g = self.grid.handle
-        stream = torch.cuda.current_stream().cuda_stream
         scale = -1.0 / (self.dt * self.dt)
         if self.k == 0:
             hist = self.hist
+            gp = self.grad.slots[0].data_ptr()
             for n in range(self.nt - 1, -1, -1):
-                self.adj.apply(n, 1, self.dt)
                 if n >= 1:
-                    fd.fd_imaging_accumulate(g, scale, self.mu.slots[n % 2].data_ptr(), hist[n + 1].data_ptr(),
-                                             hist[n].data_ptr(), hist[n - 1].data_ptr(),
-                                             self.grad.slots[0].data_ptr(), stream)
+                    fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, hist[n + 1].data_ptr(),
+                                                 hist[n].data_ptr(), hist[n - 1].data_ptr(), gp)
+                else:
+                    self.adj.apply(n, 1, self.dt)
             return self.grad.data
         k = self.k
         seg = self.seg
@@ -160,12 +160,13 @@ class Propagator:
                 fd.fd_operator_step(self.re.handle, t, self.dt, seg[i].data_ptr(), seg[i - 1].data_ptr(),
                                     seg[i + 1].data_ptr())
             for n in range(n_hi - 1, n_lo - 1, -1):
-                self.adj.apply(n, 1, self.dt)
                 if n >= 1:
                     i = n - (n_lo - 2)
-                    fd.fd_imaging_accumulate(g, scale, self.mu.slots[n % 2].data_ptr(), seg[i].data_ptr(),
-                                             seg[i - 1].data_ptr(), seg[i - 2].data_ptr(),
-                                             self.grad.slots[0].data_ptr(), stream)
+                    fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, seg[i].data_ptr(),
+                                                 seg[i - 1].data_ptr(), seg[i - 2].data_ptr(),
+                                                 self.grad.slots[0].data_ptr())
+                else:
+                    self.adj.apply(n, 1, self.dt)
         return self.grad.data
 
 

@@ -131,7 +131,7 @@ def case_conv(args):
     ws.h[0][:, 6:].zero_()
     st = torch.cuda.current_stream().cuda_stream
     for _ in range(args.reps):
-        closure.network_forward(net, ws, st)
+        closure.network_forward(net, ws, st, tensor_memory=False)
     _sync()
 
 

@@ -361,18 +361,21 @@ def test_training_lowers_loss_and_trace_error():
     assert np.isfinite(learned) and learned < 0.85 * plain, (learned, plain)
 
 
-@pytest.mark.parametrize("cin,cout,relu,mask,flip,f32", [(6, 16, True, False, 0, False), (16, 16, False, True, 0, False),
-                                                        (16, 5, True, True, 0, False), (16, 1, False, False, 0, True),
-                                                        (16, 16, False, True, 1, False), (6, 16, False, False, 1, False)])
-def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32):
+@pytest.mark.parametrize("cin,cout,relu,mask,flip,f32,shape", [
+    (6, 16, True, False, 0, False, (19, 7, 150)), (16, 16, False, True, 0, False, (19, 7, 150)),
+    (16, 5, True, True, 0, False, (19, 7, 150)), (16, 1, False, False, 0, True, (19, 7, 150)),
+    (16, 16, False, True, 1, False, (19, 7, 150)), (6, 16, False, False, 1, False, (19, 7, 150)),
+    (16, 16, True, False, 0, False, (70, 6, 260)), (16, 16, True, False, 0, False, (64, 17, 128)),
+    (6, 16, True, False, 0, False, (1, 1, 1))])
+def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32, shape):
     """The tcgen05 kernel gives the mma.sync kernel's results bit for bit
     (both accumulate each tap's 16-term products in FP32 in the same order)
     and so the oracle parity; shapes ragged against its 2-row x 128-point
-    tiles and 16-plane chunks."""
+    tile columns, with one (tile column, plane) item per CTA and with CTA
+    shares of several planes that cross tile columns."""
     torch = _torch()
     fd = _fd()
     st = torch.cuda.current_stream().cuda_stream
-    shape = (19, 7, 150)
     g = np.random.default_rng(400 + cin + cout + flip)
     nin = cout if flip else cin  # channels the convolution reads
     nout = cin if flip else cout

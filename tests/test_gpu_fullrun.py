@@ -1,0 +1,68 @@
+"""Full-run parity gate at the configured size: the 512^3 two-layer workload
+(10 m, 40-cell sponge, one 10 Hz Ricker source at the surface centre,
+101 x 101 receivers, dt at CFL 0.4, 1000 steps) run from rest through
+AcousticModel.forward -- the host-buffer call the end-to-end benchmark times,
+on the tiling the benchmark's autotuner picks -- against expected values
+written by tests/golden/make_fullrun_traces.py, which calls only the FP64
+oracle (the forward operator of the paper's Seismic Inversion Example as a
+plain loop nest).
+
+Checked, element by element against the stored values:
+  * the receiver traces rec[n][p] of a fixed, seeded subset of 512 of the
+    10 201 receivers over all 1000 steps: relative L2 <= 1e-4 (the gate);
+  * the final field u^1000 on every 8th node along each axis (64^3 nodes)
+    and its L2 norm over the whole grid: relative error <= 1e-4.
+The stored values are the FP64 results rounded to FP32 (a relative change of
+at most 6e-8 per value, far below the tolerance).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from fdrun import rel_l2
+from paper_1707_03776_gb300 import workloads as wl
+from paper_1707_03776_gb300.modeling import AcousticModel
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = 1e-4
+
+
+def _golden(so):
+    path = os.path.join(HERE, "golden", "fullrun_512_so%d_nt1000.npz" % so)
+    if not os.path.exists(path):
+        pytest.skip("no stored FP64 oracle run for SO%d" % so)
+    return np.load(path)
+
+
+@pytest.mark.parametrize("so", [8, 4, 16])
+def test_fullrun_matches_fp64_oracle(so):
+    import torch
+    g = _golden(so)
+    cfg = wl.acoustic_config(n=512, space_order=so, nt=1000)
+    assert int(g["n"]) == 512 and int(g["so"]) == so and int(g["nt"]) == cfg["nt"]
+    assert float(g["dt"]) == cfg["dt"]
+    model = AcousticModel(cfg["shape"], cfg["spacing"], cfg["origin"], so, cfg["src_coords"], cfg["rec_coords"],
+                          cfg["nt"])
+    m_h = torch.from_numpy(cfg["m"]).pin_memory()
+    eta_h = torch.from_numpy(cfg["eta"]).pin_memory()
+    src_h = torch.from_numpy(cfg["src_trace"]).pin_memory()
+    model.load(m_h, eta_h, src_h)
+    model.autotune(cfg["dt"])
+    rec = model.forward(m_h, eta_h, src_h, cfg["dt"]).numpy()
+    idx = g["rec_index"].astype(np.int64)
+    ref = g["traces"].astype(np.float64)
+    assert np.abs(ref).max() > 0
+    err_rec = rel_l2(rec[:, idx], ref)
+    u = model.u.at(cfg["nt"])
+    s = int(g["field_stride"])
+    field = u[::s, ::s, ::s].cpu().numpy()
+    err_field = rel_l2(field, g["field_sub"].astype(np.float64))
+    norm = float(torch.linalg.vector_norm(u.double()).item())
+    err_norm = abs(norm - float(g["field_norm"])) / float(g["field_norm"])
+    print("SO%d: traces %.3e, field samples %.3e, field norm %.3e" % (so, err_rec, err_field, err_norm))
+    assert err_rec <= TOL, err_rec
+    assert err_field <= TOL, err_field
+    assert err_norm <= TOL, err_norm

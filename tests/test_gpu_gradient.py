@@ -106,3 +106,50 @@ def test_step_out_of_place_matches_apply():
     op.apply(0, 1, 1e-3)
     op.sync()
     np.testing.assert_array_equal(out[..., :70].cpu().numpy(), u.at(1).cpu().numpy())
+
+
+@pytest.mark.parametrize("flags", [0, fd.FD_FLAG_REVERSE, fd.FD_FLAG_PLAIN_KERNELS | fd.FD_FLAG_REVERSE])
+def test_fused_imaging_equals_step_then_imaging(flags):
+    """fd_operator_apply_imaging (the imaging condition accumulated inside the
+    tiled sweep, or after the step on the plain kernels) equals the step
+    followed by fd_imaging_accumulate bit for bit, sources included."""
+    import torch
+    shape = (22, 37, 70)
+    h = (10.0,) * 3
+    origin = (0.0,) * 3
+    nt, n, dt = 6, 3, 1e-3
+    m = np.full(shape, 1.0 / 2000.0 ** 2, dtype=np.float32)
+    grid = fd.Grid(shape, h, origin)
+    src_c = wl.random_points(shape, h, origin, 3, 11, margin=1.0)
+    trace = np.random.default_rng(12).standard_normal((nt, 3)).astype(np.float32)
+    fields = [torch.zeros(grid.padded_shape, dtype=torch.float32, device="cuda") for _ in range(4)]
+    for i, f in enumerate(fields):
+        f[..., :shape[2]].copy_(torch.from_numpy(wl.random_field(shape, 20 + i, smooth=1)))
+    u0, u1, u2, grad0 = fields
+    state = [wl.random_field(shape, 30 + i, smooth=1) for i in range(2)]
+    written = n % 2 if flags & fd.FD_FLAG_REVERSE else (n + 1) % 2
+    out = []
+    for fused in (True, False):
+        u = fd.TimeData("u", grid)
+        md = fd.DenseData("m", grid)
+        md.data.copy_(torch.from_numpy(m))
+        src = fd.PointData("src", grid, src_c, nt)
+        src.data[:, :3].copy_(torch.from_numpy(trace))
+        op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, 8, u, md, src=src, flags=flags)
+        for s, v in zip(u.slots, state):
+            s[..., :shape[2]].copy_(torch.from_numpy(v))
+        grad = grad0.clone()
+        scale = -1.0 / dt ** 2
+        if fused:
+            fd.fd_operator_apply_imaging(op.handle, n, dt, scale, u0.data_ptr(), u1.data_ptr(), u2.data_ptr(),
+                                         grad.data_ptr())
+        else:
+            op.apply(n, 1, dt)
+            fd.fd_imaging_accumulate(grid.handle, scale, u.slots[written].data_ptr(), u0.data_ptr(), u1.data_ptr(),
+                                     u2.data_ptr(), grad.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        op.sync()
+        torch.cuda.synchronize()
+        out.append((u.slots[written][..., :shape[2]].cpu().numpy(), grad[..., :shape[2]].cpu().numpy()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert np.abs(out[0][1] - grad0[..., :shape[2]].cpu().numpy()).max() > 0
