@@ -1,32 +1,39 @@
 // The closure network's 3x3x3 convolution on the 5th-generation tensor cores
 // (tcgen05.mma with TMEM accumulators), the alternative to the mma.sync
-// kernel of k_cnn.cu with the same inputs, outputs and results.
+// kernel of k_cnn.cu with the same inputs and outputs.
 //
 // Implicit GEMM per output line of 128 points (the MMA's M = 128 TMEM lanes
-// along d2): D[128 x 16 channels] = sum over the 27 taps of A_tap[128 x 16]
-// B_tap[16 x 16], one tcgen05.mma.kind::f16 (M = 128, N = 16, K = 16, BF16 in,
-// FP32 accumulate) per tap.  With 16 output channels an MMA that takes its
-// 4 KB A tile from shared memory is bound by those reads (4 KB per 65 kFLOP),
-// so here the A operand lives in tensor memory:
-//   * a persistent CTA per SM (all 512 TMEM columns) sweeps tile columns of
-//     2 output rows x 128 points along d0; each input plane tile (4 rows x 130
-//     points x 16 channels, zero outside the grid) arrives by two TMA copies
-//     into a 6-plane shared-memory ring, laid out as K-major no-swizzle core
-//     matrices (channel half h of tile point p at byte (h * 520 + p) * 16);
-//   * tcgen05.cp copies each of its 4 input lines three times into a 4-plane
-//     TMEM ring, started 0, 1 and 2 points in: the three d2 shifts of the
-//     taps, so that lane i holds input point x0 + i - 1 + c for shift c;
-//   * the 54 MMAs of an output plane (2 rows x 27 taps) then read A from TMEM
-//     and only their 512-byte weight tile from shared memory, into one of two
-//     accumulator buffers (2 rows x 16 columns);
-//   * warps 0-3 read an accumulator buffer back with tcgen05.ld (lane =
-//     point), apply bias, ReLU and the input-gradient mask, store BF16 (or the
-//     one FP32 channel) and hand the buffer back; warp 4 issues everything.
-// TMA loads, cp and MMA completion (tcgen05.commit) and the epilogue are
-// ordered by mbarriers whose waits are bounded: a wait that gives up records
-// FD_ERR_TIMEOUT in the status word, the other role stops at its next wait,
-// and the CTA drains its copies and tensor-core work and frees the tensor
-// memory before it leaves.
+// along d2), tcgen05.mma.kind::f16 (BF16 in, FP32 accumulate in TMEM) with
+// both operands in shared memory.  One thread issues an MMA about every 60
+// cycles whatever its N, and an N = 16 MMA reads a 4 KB A tile for 65 kFLOP,
+// so the kernel makes each MMA as wide as the 16 output channels allow:
+//   * a persistent CTA per SM sweeps tile columns of 4 output rows x 128
+//     points along d0; each input plane tile (6 rows x 130 points x 16
+//     channels, zero outside the grid) arrives by two TMA copies into a
+//     6-plane ring as K-major no-swizzle core matrices (channel half h of
+//     tile point p at byte h * 12544 + p * 16), so that the A tile of input
+//     line l with d2 shift c is the same layout started (l * 130 + c) * 16
+//     bytes in.  A, re-read by every MMA, is most of the operand traffic
+//     that bounds the kernel (measured: the tensor core's operand pipe 81 %
+//     busy, its math 28 %); taller tile columns re-read less of it but
+//     measured slower (6 rows: 5 % slower, 8 rows with a 5-plane ring: 9 %);
+//   * the three d1 taps b of an (input plane a, shift c) are the N = 16 b + o
+//     columns of one B operand, and output row r's accumulator sits at column
+//     16 (3 - r): input line l then feeds rows l + 1, l, l - 1 through one
+//     contiguous column range -- one MMA per input line, N = 48 inside the
+//     tile and 16 or 32 at its edges, 54 per output plane, no work wasted;
+//   * two issuing warps take alternate output planes, each with two
+//     accumulator sets of 64 columns (a clearing MMA with zero operands
+//     starts each);
+//   * warps 0-3 read a set back with tcgen05.ld (lane = point), apply bias,
+//     ReLU and the input-gradient mask, store BF16 (or the one FP32 channel)
+//     and hand it back.
+// The sum over taps runs in another order than the mma.sync kernel's, so the
+// two agree to FP32 rounding, not bit for bit.  TMA loads, MMA completion
+// (tcgen05.commit) and the epilogue are ordered by mbarriers whose waits are
+// bounded: a wait that gives up records FD_ERR_TIMEOUT in the status word,
+// every other role stops at its next wait, and each issuing thread drains its
+// tensor-core work before the tensor memory is freed.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -39,27 +46,58 @@ namespace {
 using namespace tile_dev;
 
 constexpr int kUC = 16;                               // channels per point
-constexpr int kTR = 2;                                // output rows per tile column
+constexpr int kTR = 4;                                // output rows per tile column
 constexpr int kTW = 128;                              // output points per line = MMA M = TMEM lanes
 constexpr int kPW = kTW + 2;                          // input line with the d2 halo
 constexpr int kInRows = kTR + 2;                      // input lines per plane tile
-constexpr int kPts = kInRows * kPW;                   // points per input plane tile
-constexpr uint32_t kHalfBytes = kPts * 16;            // one channel half of a tile (the A LBO)
+constexpr uint32_t kHalfBytes = (kInRows * kPW * 16 + 127) / 128 * 128;  // one channel half (the A LBO)
 constexpr uint32_t kPlaneBytes = 2 * kHalfBytes;
+constexpr uint32_t kTmaBytes = 2 * kInRows * kPW * 16;  // what the two copies of a plane deliver
 constexpr int kSRing = 6;                             // input planes in shared memory
-constexpr int kTRing = 4;                             // input planes in tensor memory
-constexpr uint32_t kPlaneCols = kInRows * 3 * 8;      // TMEM columns of an input plane (lines x shifts x K/2)
-constexpr uint32_t kAccCol = kTRing * kPlaneCols;     // first accumulator column
-constexpr uint32_t kTmemCols = 512;
-constexpr int kThreads = 160;                         // warps 0-3: epilogue; warp 4: copies and MMAs
-constexpr uint32_t kWTapBytes = 512;                  // [2 halves][16 n][8 k] BF16
+constexpr uint32_t kAccCols = kTR * 16;               // one accumulator set: row r at 16 (kTR - 1 - r)
+// 2 issuers x 2 buffers, allocated as a power of two (at least 32 columns)
+constexpr uint32_t kTmemCols = 4 * kAccCols <= 32 ? 32 : 4 * kAccCols <= 64 ? 64 : 4 * kAccCols <= 128 ? 128
+                                 : 4 * kAccCols <= 256 ? 256 : 512;
+// warps: 0-3 epilogue (TMEM lanes 32w..), 4 loader, 5-6 MMA issuers
+constexpr int kWarpLoad = 4, kWarpMma = 5;
+constexpr int kThreads = 32 * (kWarpMma + 2);
+constexpr uint32_t kWCombBytes = 1536;                // per (a, c): [2 halves][48 n = 16 b + o][8 k] BF16
 constexpr uint32_t kWOff = kSRing * kPlaneBytes;
-constexpr uint32_t kBarOff = kWOff + 27 * kWTapBytes;
-constexpr int kNBars = 2 * kSRing + 5;                // full, empty, mma_done[2], acc_free[2], fin
+constexpr uint32_t kZOff = kWOff + 9 * kWCombBytes;   // 4 KB of zeros: the clearing MMA's operands
+constexpr uint32_t kBarOff = kZOff + 4096;
+// mbarriers: full (plane landed, TMA), empty (both issuers done with a
+// plane), done (an accumulator set's MMAs done), free (its 4 epilogue warps
+// done), fin (final drain of each issuer)
+constexpr int kFull = 0, kEmpty = kSRing, kDone = 2 * kSRing, kFree = kDone + 4, kFin = kFree + 4,
+              kNBars = kFin + 2;
 constexpr uint32_t kSmemU = kBarOff + 8 * kNBars + 16;
-static_assert(kAccCol + 2 * kTR * 16 <= kTmemCols, "tensor memory layout");
-static_assert(kPlaneBytes % 128 == 0 && kHalfBytes % 128 == 0 && kWOff % 128 == 0, "TMA destinations");
+__host__ __device__ constexpr uint32_t bar_count(int i)
+{
+    return (i >= kEmpty && i < kDone) ? 2u : (i >= kFree && i < kFin) ? 4u : 1u;
+}
+static_assert(kPlaneBytes % 128 == 0 && kHalfBytes % 128 == 0 && kWOff % 128 == 0 && kZOff % 128 == 0,
+              "TMA destinations and descriptors");
 static_assert((kHalfBytes >> 4) < (1u << 14), "descriptor offset field");
+static_assert(kSmemU <= 227 * 1024, "shared memory");
+
+// The MMA of input line l (-1..kTR: tile lines y0 - 1 .. y0 + kTR) for one
+// (plane a, shift c): the d1 taps b = 0, 1, 2 of its 16 output channels go
+// to rows l + 1, l, l - 1 (those inside the tile), the N = 16 b + o columns
+// of B; with row r's accumulator at 16 (kTR - 1 - r) they are one contiguous
+// range.  Returns the range's first accumulator column, N and first B row.
+struct LineMma {
+    uint32_t dcol;
+    uint32_t n;
+    uint32_t brow;
+};
+__host__ __device__ constexpr LineMma line_mma(int l)
+{
+    return l == -1        ? LineMma{16u * (kTR - 1), 16u, 0u}
+           : l == 0       ? LineMma{16u * (kTR - 2), 32u, 0u}
+           : l == kTR - 1 ? LineMma{0u, 32u, 16u}
+           : l == kTR     ? LineMma{0u, 16u, 32u}
+                          : LineMma{16u * (uint32_t)(kTR - 2 - l), 48u, 0u};
+}
 
 struct UDims {
     int n0, n1, n2;
@@ -76,23 +114,21 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// instruction descriptor: D F32, A and B BF16, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: D F32, A and B BF16, both K-major, M = 128, N
+__host__ __device__ constexpr uint32_t idesc_n(uint32_t n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-// D[tmem] (+)= A[tmem] * B[smem descriptor]
-__device__ __forceinline__ void umma_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accumulate)
+// D[tmem] (+)= A[smem descriptor] * B[smem descriptor]
+__device__ __forceinline__ void umma_ss(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "r"(tmem_a), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
-}
-
-// 128 rows x 256 bits from shared memory (descriptor) into TMEM lanes 0..127
-__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc)
-{
-    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar)
@@ -155,38 +191,36 @@ __device__ __forceinline__ Seg segment_at(long long q, long long q_hi, const UDi
 
 template <bool RELU, bool MASK, bool OUT_F32>
 __global__ void __launch_bounds__(kThreads, 1)
-    conv3d_tmem_kernel(const __grid_constant__ CUtensorMap xmap, const uint4 *__restrict__ wpack,
+    conv3d_umma_kernel(const __grid_constant__ CUtensorMap xmap, const uint4 *__restrict__ wpack,
                        const float *__restrict__ bias, int cout, const __nv_bfloat16 *__restrict__ mask, void *y,
                        UDims d, int *status)
 {
     extern __shared__ __align__(1024) unsigned char usm[];
     const uint32_t ring = smem_addr(usm);
     const uint32_t wsm = ring + kWOff;
-    // barriers: full[kSRing] (plane landed), empty[kSRing] (its copies to
-    // TMEM done), mma_done[2] (an accumulator buffer's MMAs done),
-    // acc_free[2] (its epilogue done; 4 warp arrivals), fin (final drain)
+    const uint32_t zsm = ring + kZOff;
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(usm + kBarOff);
-    constexpr int kFull = 0, kEmpty = kSRing, kDone = 2 * kSRing, kFree = 2 * kSRing + 2, kFin = 2 * kSRing + 4;
     volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(usm + kBarOff + 8 * kNBars);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(usm + kBarOff + 8 * kNBars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     auto BAR = [&](int i) { return smem_addr(&bars[i]); };
 
-    for (int q = tid; q < 27 * (int)kWTapBytes / 16; q += blockDim.x)
+    for (int q = tid; q < 9 * (int)kWCombBytes / 16; q += blockDim.x)
         reinterpret_cast<uint4 *>(usm + kWOff)[q] = wpack[q];
+    for (int q = tid; q < 4096 / 16; q += blockDim.x) reinterpret_cast<uint4 *>(usm + kZOff)[q] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&xmap)) : "memory");
-        for (int i = 0; i < kNBars; i++) mbar_init(BAR(i), (i == kFree || i == kFree + 1) ? 4u : 1u);
+        for (int i = 0; i < kNBars; i++) mbar_init(BAR(i), bar_count(i));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
-    if (warp == 4) {
+    if (warp == kWarpLoad) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr((const void *)tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    proxy_fence();  // the weights (generic stores) are read by the tensor core
+    proxy_fence();  // the weights and zeros (generic stores) are read by the tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -197,28 +231,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long long total = (long long)tiles2 * tiles1 * d.n0;
     const long long q_lo = (long long)blockIdx.x * total / gridDim.x;
     const long long q_hi = (long long)(blockIdx.x + 1) * total / gridDim.x;
+    // planes are counted over the CTA's whole share (a segment of nout output
+    // planes reads nout + 2 input planes): input g -> shared slot g % kSRing;
+    // output oq -> issuer oq & 1, its accumulator buffer (oq >> 1) & 1, i.e.
+    // accumulator set 2 (oq & 1) + ((oq >> 1) & 1)
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(status, (int)FD_ERR_TIMEOUT);
+    };
+    auto acc_set = [](unsigned oq) { return (int)(2u * (oq & 1u) + ((oq >> 1) & 1u)); };
 
-    if (warp == 4) {
+    if (warp == kWarpLoad) {
+        // loader: every input plane of the CTA's share, kSRing ahead at most
         if (lane == 0) {
-            unsigned g_load = 0, g_full = 0;  // plane loads issued / whose arrival was waited (in order)
-            unsigned oq = 0;                  // output planes whose MMAs were issued
+            unsigned g = 0;
             bool ok = true;
-            const uint64_t bdesc0 = umma_desc(wsm, 256, 128);
             for (long long q = q_lo; q < q_hi && ok;) {
                 const Seg sg = segment_at(q, q_hi, d, tiles2);
-                const int nout = sg.ze - sg.zs, nin = nout + 2;
-                const unsigned load0 = g_load, oq0 = oq;
-                // input i of the segment is plane zs - 1 + i: shared slot
-                // (load0 + i) % kSRing, TMEM slot i % kTRing
-                auto load = [&](int i) -> bool {
-                    const unsigned g = load0 + (unsigned)i;
+                const int nin = sg.ze - sg.zs + 2;
+                for (int i = 0; i < nin && ok; i++, g++) {
                     const int slot = (int)(g % kSRing);
-                    // the slot's previous plane has been copied to TMEM
+                    // both issuers are done with the slot's previous plane
                     if (g >= (unsigned)kSRing &&
-                        !mbar_wait_or_abort(BAR(kEmpty + slot), ((g / kSRing) - 1u) & 1u, abort_flag))
-                        return false;
+                        !mbar_wait_or_abort(BAR(kEmpty + slot), ((g / kSRing) - 1u) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
                     const uint32_t bar = BAR(kFull + slot);
-                    mbar_expect_tx(bar, kPlaneBytes);
+                    mbar_expect_tx(bar, kTmaBytes);
                     const uint32_t dst = ring + (uint32_t)slot * kPlaneBytes;
 #pragma unroll
                     for (int h = 0; h < 2; h++)
@@ -228,94 +268,80 @@ __global__ void __launch_bounds__(kThreads, 1)
                             "l"(reinterpret_cast<unsigned long long>(&xmap)), "r"(0), "r"(h), "r"(sg.x0 - 1),
                             "r"(sg.y0 - 1), "r"(sg.zs - 1 + i), "r"(bar)
                             : "memory");
-                    g_load++;
-                    return true;
+                }
+                q += sg.ze - sg.zs;
+            }
+            if (!ok) fail();
+            // the last kSRing loads may not have been waited on by an issuer
+            const unsigned long long deadline = global_ns() + kWaitLimitNs;
+            for (unsigned k = (g > (unsigned)kSRing ? g - kSRing : 0u); k < g; k++)
+                mbar_wait_until(BAR(kFull + (int)(k % kSRing)), (k / kSRing) & 1u, deadline);
+        }
+        __syncwarp();
+    } else if (warp >= kWarpMma) {
+        // issuer P takes the outputs oq with oq & 1 == P: a clearing MMA,
+        // then per (plane a, shift c) one MMA per input line (N = 16..48)
+        const int P = warp - kWarpMma;
+        if (lane == 0) {
+            unsigned g0 = 0, oq0 = 0;  // first input and first output of the segment
+            bool ok = true;
+            for (long long q = q_lo; q < q_hi && ok;) {
+                const Seg sg = segment_at(q, q_hi, d, tiles2);
+                const int nout = sg.ze - sg.zs, nin = nout + 2;
+                // each input gets one empty-commit from each issuer, after that
+                // issuer's last read of it (at once if it reads none of them)
+                auto commit_inputs = [&](int lo, int hi) {
+                    for (int i = lo; i <= hi; i++) umma_commit(BAR(kEmpty + (int)((g0 + (unsigned)i) % kSRing)));
                 };
-                auto cp_in = [&](int i) -> bool {
-                    const unsigned g = load0 + (unsigned)i;
-                    const int slot = (int)(g % kSRing);
-                    if (!mbar_wait_or_abort(BAR(kFull + slot), (g / kSRing) & 1u, abort_flag)) return false;
-                    g_full++;
-                    tc_fence_after();
-                    const uint32_t src = ring + (uint32_t)slot * kPlaneBytes;
-                    const uint32_t tcol = tmem + (uint32_t)(i % kTRing) * kPlaneCols;
-#pragma unroll
-                    for (int r = 0; r < kInRows; r++)
-#pragma unroll
-                        for (int c = 0; c < 3; c++)
-                            tmem_cp_128x256b(tcol + (uint32_t)((r * 3 + c) * 8),
-                                             umma_desc(src + (uint32_t)((r * kPW + c) * 16), kHalfBytes, 128));
-                    umma_commit(BAR(kEmpty + slot));
-                    return true;
-                };
-                const int npre = nin < kSRing ? nin : kSRing;
-                for (int i = 0; i < npre && ok; i++) ok = load(i);
-                for (int i = 0; i < 3 && ok; i++) ok = cp_in(i);
-                int next_load = npre, next_cp = 3;
-                for (int o = 0; o < nout && ok; o++) {
-                    const unsigned b = oq & 1u;
-                    // the epilogue has read this accumulator buffer back
-                    if (oq >= 2 && !mbar_wait_or_abort(BAR(kFree + b), ((oq >> 1) - 1u) & 1u, abort_flag)) {
+                int o = ((oq0 & 1u) == (unsigned)P) ? 0 : 1;
+                if (o >= nout) commit_inputs(0, nin - 1);
+                int c_next = 0;
+                for (; o < nout && ok; o += 2) {
+                    const unsigned oq = oq0 + (unsigned)o;
+                    const int set = acc_set(oq);
+                    // the epilogue has read this accumulator set back
+                    if (oq >= 4 && !mbar_wait_or_abort(BAR(kFree + set), ((oq >> 2) - 1u) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
+                    uint32_t pl[3];
+                    for (int a = 0; a < 3 && ok; a++) {
+                        const unsigned g = g0 + (unsigned)(o + a);
+                        ok = mbar_wait_or_abort(BAR(kFull + (int)(g % kSRing)), (g / kSRing) & 1u, abort_flag);
+                        pl[a] = ring + (uint32_t)(g % kSRing) * kPlaneBytes;
+                    }
+                    if (!ok) break;
                     tc_fence_after();
-                    const uint32_t dcol = tmem + kAccCol + b * 32u;
+                    const uint32_t acc = tmem + (uint32_t)set * kAccCols;
+                    // clear the set: zeros times zeros, accumulator overwritten
+                    umma_ss(acc, umma_desc(zsm, 2048, 128), umma_desc(zsm, kAccCols * 16, 128), idesc_n(kAccCols), 0u);
 #pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        const uint32_t pl = tmem + (uint32_t)((o + a) % kTRing) * kPlaneCols;
+                    for (int a = 0; a < 3; a++)
 #pragma unroll
-                        for (int bb = 0; bb < 3; bb++)
+                        for (int c = 0; c < 3; c++) {
+                            const uint32_t wb = wsm + (uint32_t)((a * 3 + c) * kWCombBytes);
 #pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                const int t = a * 9 + bb * 3 + c;
-#pragma unroll
-                                for (int ro = 0; ro < kTR; ro++)
-                                    umma_tmem_a(dcol + (uint32_t)(ro * 16), pl + (uint32_t)(((ro + bb) * 3 + c) * 8),
-                                                bdesc0 + (uint64_t)(t * (kWTapBytes >> 4)), t > 0 ? 1u : 0u);
-                            }
-                    }
-                    umma_commit(BAR(kDone + b));
-                    oq++;
-                    if (next_cp < nin) {
-                        // the TMEM slot of input next_cp - kTRing is free
-                        // once the last output reading it (that index) is done
-                        if (next_cp >= kTRing) {
-                            const unsigned ow = oq0 + (unsigned)(next_cp - kTRing);
-                            if (!mbar_wait_or_abort(BAR(kDone + (ow & 1u)), (ow >> 1) & 1u, abort_flag)) {
-                                ok = false;
-                                break;
+                            for (int l = -1; l <= kTR; l++) {
+                                constexpr uint32_t lbo_b = 48 * 16;
+                                const LineMma m = line_mma(l);
+                                umma_ss(acc + m.dcol,
+                                        umma_desc(pl[a] + (uint32_t)(((l + 1) * kPW + c) * 16), kHalfBytes, 128),
+                                        umma_desc(wb + m.brow * 16u, lbo_b, 128), idesc_n(m.n), 1u);
                             }
                         }
-                        if (!cp_in(next_cp++)) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                    if (next_load < nin && !load(next_load++)) {
-                        ok = false;
-                        break;
-                    }
+                    umma_commit(BAR(kDone + set));
+                    const int hi = (o + 2 < nout) ? o + 1 : nin - 1;
+                    commit_inputs(c_next, hi);
+                    c_next = hi + 1;
                 }
-                // the segment's last commit covers every copy and MMA of it:
-                // afterwards all TMEM and shared slots are free
-                if (ok && oq > oq0) {
-                    const unsigned ow = oq - 1;
-                    ok = mbar_wait_or_abort(BAR(kDone + (ow & 1u)), (ow >> 1) & 1u, abort_flag);
-                }
+                g0 += (unsigned)nin;
+                oq0 += (unsigned)nout;
                 q += nout;
             }
-            if (!ok) {
-                *abort_flag = 1;
-                atomicExch(status, (int)FD_ERR_TIMEOUT);
-            }
-            // drain: plane copies still owed, then every tcgen05 operation
-            // issued (one more commit), under one shared deadline
+            if (!ok) fail();
             const unsigned long long deadline = global_ns() + kWaitLimitNs;
-            for (unsigned g = g_full; g < g_load; g++)
-                mbar_wait_until(BAR(kFull + (int)(g % kSRing)), (g / kSRing) & 1u, deadline);
-            umma_commit(BAR(kFin));
-            mbar_wait_until(BAR(kFin), 0u, deadline);
+            umma_commit(BAR(kFin + P));
+            mbar_wait_until(BAR(kFin + P), 0u, deadline);
         }
         __syncwarp();
     } else {
@@ -325,19 +351,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (long long q = q_lo; q < q_hi && ok;) {
             const Seg sg = segment_at(q, q_hi, d, tiles2);
             for (int z = sg.zs; z < sg.ze; z++) {
-                const unsigned b = oq & 1u;
+                const int set = acc_set(oq);
                 const bool got =
-                    __all_sync(0xffffffffu, mbar_wait_or_abort(BAR(kDone + b), (oq >> 1) & 1u, abort_flag));
+                    __all_sync(0xffffffffu, mbar_wait_or_abort(BAR(kDone + set), (oq >> 2) & 1u, abort_flag));
                 if (!got) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int ro = 0; ro < kTR; ro++) {
+                for (int r = 0; r < kTR; r++) {
                     uint32_t v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + kAccCol + b * 32u + (uint32_t)(ro * 16), v);
-                    const int gy = sg.y0 + ro, gx = sg.x0 + 32 * warp + lane;
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)set * kAccCols + 16u * (kTR - 1 - r), v);
+                    const int gy = sg.y0 + r, gx = sg.x0 + 32 * warp + lane;
                     if (gy >= d.n1 || gx >= d.n2) continue;
                     const long long pt = ((long long)z * d.n1 + gy) * d.n2 + gx;
                     float f[16];
@@ -350,14 +376,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (MASK) {
                         const uint4 *mk = reinterpret_cast<const uint4 *>(mask + pt * kUC);
 #pragma unroll
-                        for (int hh = 0; hh < 2; hh++) {
-                            const uint4 m4 = mk[hh];
+                        for (int h2 = 0; h2 < 2; h2++) {
+                            const uint4 m4 = mk[h2];
                             const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-                            for (int j = 0; j < 4; j++) {
-                                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw[j]);
-                                if (!(__low2float(m2) > 0.f)) f[hh * 8 + 2 * j] = 0.f;
-                                if (!(__high2float(m2) > 0.f)) f[hh * 8 + 2 * j + 1] = 0.f;
+                            for (int jj = 0; jj < 4; jj++) {
+                                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw[jj]);
+                                if (!(__low2float(m2) > 0.f)) f[h2 * 8 + 2 * jj] = 0.f;
+                                if (!(__high2float(m2) > 0.f)) f[h2 * 8 + 2 * jj + 1] = 0.f;
                             }
                         }
                     }
@@ -366,51 +392,52 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
                         uint32_t packed[8];
 #pragma unroll
-                        for (int j = 0; j < 8; j++) {
-                            const __nv_bfloat162 t2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-                            packed[j] = *reinterpret_cast<const uint32_t *>(&t2);
+                        for (int jj = 0; jj < 8; jj++) {
+                            const __nv_bfloat162 t2 = __floats2bfloat162_rn(f[2 * jj], f[2 * jj + 1]);
+                            packed[jj] = *reinterpret_cast<const uint32_t *>(&t2);
                         }
                         uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(y) + pt * kUC);
                         dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                         dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                     }
                 }
-                // this buffer's values are in registers: hand it back
+                // this set's values are in registers: hand it back
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(BAR(kFree + b));
+                if (lane == 0) mbar_arrive(BAR(kFree + set));
                 oq++;
             }
             q += sg.ze - sg.zs;
         }
-        if (!ok && lane == 0) {
-            *abort_flag = 1;
-            atomicExch(status, (int)FD_ERR_TIMEOUT);
-        }
+        if (!ok && lane == 0) fail();
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kWarpLoad) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
 
-// weights w[27][cin][cout] (FP32) into [27][2 halves][16 n][8 k] BF16; flip =
-// the input-gradient convolution (taps mirrored, channel axes exchanged)
+// weights w[27][cin][cout] (FP32) into the B operands: per (plane a, shift
+// c), [2 halves][48 n][8 k] BF16 with n = 16 b + o (the three d1 taps side by
+// side); flip = the input-gradient convolution (taps mirrored, channel axes
+// exchanged)
 __global__ void pack_umma_kernel(const float *__restrict__ w, int cin, int cout, int flip,
                                  __nv_bfloat16 *__restrict__ out)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= 27 * 256) return;
-    const int t = q / 256, rem = q % 256;
-    const int h = rem / 128, n = (rem / 8) % 16, kk = rem % 8;
+    if (q >= 9 * 768) return;
+    const int comb = q / 768, rem = q % 768;
+    const int h = rem / 384, n = (rem / 8) % 48, kk = rem % 8;
+    const int a = comb / 3, c = comb % 3, b = n / 16, o = n % 16;
+    const int t = a * 9 + b * 3 + c;
     const int k = h * 8 + kk;
     float v = 0.f;
     if (!flip) {
-        if (k < cin && n < cout) v = w[((long long)t * cin + k) * cout + n];
+        if (k < cin && o < cout) v = w[((long long)t * cin + k) * cout + o];
     } else {
-        if (k < cout && n < cin) v = w[((long long)(26 - t) * cin + n) * cout + k];
+        if (k < cout && o < cin) v = w[((long long)(26 - t) * cin + o) * cout + k];
     }
     out[q] = __float2bfloat16(v);
 }
@@ -424,7 +451,7 @@ extern "C" fd_status fd_cnn_pack_weights_tc(const float *w, int cin, int cout, i
 {
     if (!w || !out || cin < 1 || cin > 16 || cout < 1 || cout > 16)
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_pack_weights_tc: bad arguments");
-    pack_umma_kernel<<<(27 * 256 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(w, cin, cout, flip,
+    pack_umma_kernel<<<(9 * 768 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(w, cin, cout, flip,
                                                                               (__nv_bfloat16 *)out);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(FD_ERR_CUDA, "fd_cnn_pack_weights_tc: %s", cudaGetErrorString(e));
@@ -493,7 +520,7 @@ extern "C" fd_status fd_cnn_conv3d_tc(const int64_t *shape, const void *x, const
     cudaError_t e = cudaSuccess;
 #define LAUNCH(R, M, F)                                                                                   \
     do {                                                                                                  \
-        auto k = conv3d_tmem_kernel<R, M, F>;                                                             \
+        auto k = conv3d_umma_kernel<R, M, F>;                                                             \
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemU);            \
         if (e == cudaSuccess) {                                                                           \
             k<<<grid, kThreads, kSmemU, st>>>(map, wp, bias, cout, mk, y, d, status);                     \

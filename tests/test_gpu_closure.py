@@ -368,11 +368,13 @@ def test_training_lowers_loss_and_trace_error():
     (16, 16, True, False, 0, False, (70, 6, 260)), (16, 16, True, False, 0, False, (64, 17, 128)),
     (6, 16, True, False, 0, False, (1, 1, 1))])
 def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32, shape):
-    """The tcgen05 kernel gives the mma.sync kernel's results bit for bit
-    (both accumulate each tap's 16-term products in FP32 in the same order)
-    and so the oracle parity; shapes ragged against its 2-row x 128-point
-    tile columns, with one (tile column, plane) item per CTA and with CTA
-    shares of several planes that cross tile columns."""
+    """The tcgen05 kernel against the oracle (BF16 operands, exact sums) and
+    against the mma.sync kernel: both accumulate in FP32, the tcgen05 one as
+    two tap halves added at the end, so the two differ by FP32 rounding --
+    at most one BF16 rounding step of the stored outputs, and 1e-6 relative
+    for the FP32 channel.  Shapes ragged against its 2-row x 128-point tile
+    columns, with one (tile column, plane) item per CTA and with CTA shares
+    of several planes that cross tile columns."""
     torch = _torch()
     fd = _fd()
     st = torch.cuda.current_stream().cuda_stream
@@ -401,7 +403,16 @@ def test_conv3d_tensor_memory_path(cin, cout, relu, mask, flip, f32, shape):
     fd.fd_cnn_conv3d_tc(shape, xt, frag_tc, None, nout, int(relu), mk, y2, int(f32), status, st)
     torch.cuda.synchronize()
     assert status.item() == 0
-    np.testing.assert_array_equal(y2.float().cpu().numpy(), y1.float().cpu().numpy())
+    a1, a2 = y1.float().cpu().numpy(), y2.float().cpu().numpy()
+    assert np.isfinite(a2).all()
+    if f32:
+        assert np.abs(a2 - a1).max() <= 1e-6 * np.abs(a1).max()
+    else:
+        # one BF16 step (at most 2^-7 relative) where the FP32 sums round apart, and
+        # near zero the FP32 rounding of the sum itself (its terms are up to
+        # the outputs' size)
+        bound = 2.0 ** -7 * np.abs(a1) + 1e-4 * np.abs(a1).max()
+        assert (np.abs(a2 - a1) <= bound).all(), np.abs(a2 - a1).max()
     wr = cnn.bf16_round(w).astype(np.float64)
     ref = cnn.conv3d_grad_input(xr[..., :cout], wr) if flip else cnn.conv3d(xr[..., :cin], wr, np.zeros(cout))
     if relu:
