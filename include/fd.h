@@ -407,6 +407,18 @@ fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows, int stage
 /* Steps n = t0..t0+nt-1 of every operator (receivers, update, sources as in
  * fd_operator_apply), enqueued on the operators' stream. */
 fd_status fd_batch_apply(fd_batch *batch, int64_t t0, int64_t nt, double dt);
+/* Autotuner of the batch (the GPU analogue of the paper's block-size
+ * auto-tuning, Automated code generation section): for tile heights of
+ * 10..32 rows by prefetch depths 2..4, rebuilds the batch, runs steps
+ * t0..t0+nsteps-1 of every shot timed with CUDA events on the operators'
+ * stream (after up to 3 warm-up steps), and keeps the fastest; writes the
+ * choice and its time per step (ms) when the pointers are given.  The runs
+ * advance the shots' fields and traces: tune before setting the initial
+ * state.  Drops a captured graph; synchronises the stream.  The tiling does
+ * not change any result bit.  Errors: FD_ERR_UNSUPPORTED (no tiling fits),
+ * FD_ERR_TIMEOUT, as fd_batch_apply. */
+fd_status fd_batch_autotune(fd_batch *batch, int64_t t0, int64_t nsteps, double dt, int *best_rows,
+                            int *best_stages, double *best_ms_per_step);
 /* Capture steps t0..t0+nt-1 once as a CUDA graph (on a private stream; the
  * coefficients are prepared first, outside the graph), for fd_batch_replay. */
 fd_status fd_batch_capture(fd_batch *batch, int64_t t0, int64_t nt, double dt);

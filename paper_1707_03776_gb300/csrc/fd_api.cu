@@ -1269,6 +1269,40 @@ static void batch_release(fd_batch *b)
     delete b;
 }
 
+// (Re)build the batch for a tile height and depth: every shot's tiling, then
+// the one device table of all shots.  Drops a captured graph (it holds the
+// previous table).  On failure the batch has no plan until the next build.
+static fd_status batch_build(fd_batch *b, int rows, int stages)
+{
+    if (b->has_graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->has_graph = false;
+    }
+    batch_plan_release(b->plan);
+    for (size_t i = 0; i < b->ops.size(); i++) {
+        fd_operator *op = b->ops[i];
+        fd_status s = fd_operator_set_tiling(op, rows, 0);
+        if (s != FD_OK) return s;
+        if (op->src && op->src->npoint > 0 && !op->tma.has_src)
+            return set_error(FD_ERR_UNSUPPORTED, "fd_batch: operator %d's sources do not fit the tiles", (int)i);
+    }
+    std::vector<const TmaPlan *> plans;
+    std::vector<const SparseDev *> recs;
+    std::vector<float *> rtr;
+    std::vector<long long> rst, sst;
+    std::vector<const float *> str;
+    for (fd_operator *op : b->ops) {
+        plans.push_back(&op->tma);
+        const bool hr = op->rec && op->rec->npoint > 0, hs = op->src && op->src->npoint > 0;
+        recs.push_back(hr ? &op->rec->dev : nullptr);
+        rtr.push_back(hr ? op->rec->trace : nullptr);
+        rst.push_back(hr ? op->rec->stride : 0);
+        str.push_back(hs ? op->src->trace : nullptr);
+        sst.push_back(hs ? op->src->stride : 0);
+    }
+    return batch_plan_build(b->plan, plans, recs, rtr, rst, str, sst, b->ops[0]->coef, stages, b->stream);
+}
+
 extern "C" fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows, int stages, fd_batch **out)
 {
     if (!ops || nops < 1 || !out || rows < 0 || stages < 0)
@@ -1286,14 +1320,6 @@ extern "C" fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows
         if (op->stream != ops[0]->stream)
             return set_error(FD_ERR_INVALID_ARG, "fd_batch_create: operators on different streams");
     }
-    const int want_stages = stages > 0 ? stages : 3;
-    const int want_rows = rows > 0 ? rows : 16;
-    for (int i = 0; i < nops; i++) {
-        fd_status s = fd_operator_set_tiling(ops[i], want_rows, 0);
-        if (s != FD_OK) return s;
-        if (ops[i]->src && ops[i]->src->npoint > 0 && !ops[i]->tma.has_src)
-            return set_error(FD_ERR_UNSUPPORTED, "fd_batch_create: operator %d's sources do not fit the tiles", i);
-    }
     fd_batch *b = new (std::nothrow) fd_batch();
     if (!b) return set_error(FD_ERR_NOMEM, "fd_batch_create: out of host memory");
     b->ops.assign(ops, ops + nops);
@@ -1303,21 +1329,7 @@ extern "C" fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows
     b->has_graph = false;
     b->graph_steps = 0;
     b->launches = 0;
-    std::vector<const TmaPlan *> plans;
-    std::vector<const SparseDev *> recs;
-    std::vector<float *> rtr;
-    std::vector<long long> rst, sst;
-    std::vector<const float *> str;
-    for (fd_operator *op : b->ops) {
-        plans.push_back(&op->tma);
-        const bool hr = op->rec && op->rec->npoint > 0, hs = op->src && op->src->npoint > 0;
-        recs.push_back(hr ? &op->rec->dev : nullptr);
-        rtr.push_back(hr ? op->rec->trace : nullptr);
-        rst.push_back(hr ? op->rec->stride : 0);
-        str.push_back(hs ? op->src->trace : nullptr);
-        sst.push_back(hs ? op->src->stride : 0);
-    }
-    fd_status s = batch_plan_build(b->plan, plans, recs, rtr, rst, str, sst, ops[0]->coef, want_stages, b->stream);
+    fd_status s = batch_build(b, rows > 0 ? rows : 16, stages > 0 ? stages : 3);
     if (s != FD_OK) {
         batch_release(b);
         return s;
@@ -1365,6 +1377,66 @@ extern "C" fd_status fd_batch_apply(fd_batch *b, int64_t t0, int64_t nt, double 
     fd_status s = batch_prepare(b, t0, nt, dt, "fd_batch_apply");
     if (s != FD_OK) return s;
     return batch_enqueue(b, t0, nt, b->stream);
+}
+
+extern "C" fd_status fd_batch_autotune(fd_batch *b, int64_t t0, int64_t nsteps, double dt, int *best_rows,
+                                       int *best_stages, double *best_ms_per_step)
+{
+    if (!b || nsteps < 1 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_batch_autotune: bad arguments");
+    fd_status s = batch_prepare(b, t0, nsteps, dt, "fd_batch_autotune");
+    if (s != FD_OK) return s;
+    static const int kRows[] = {10, 12, 14, 16, 20, 24, 28, 32};
+    cudaEvent_t e0, e1;
+    FD_CUDA(cudaEventCreate(&e0), "fd_batch_autotune");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(FD_ERR_CUDA, "fd_batch_autotune: cudaEventCreate");
+    }
+    int br = 0, bs = 0;
+    double bms = 1e30;
+    fd_status last = FD_OK;
+    for (int rows : kRows) {
+        for (int stages = 2; stages <= 4 && last == FD_OK; stages++) {
+            if (batch_build(b, rows, stages) != FD_OK) continue;  // does not fit: next candidate
+            last = batch_enqueue(b, t0, nsteps < 3 ? nsteps : 3, b->stream);  // warm-up
+            if (last != FD_OK) break;
+            cudaEventRecord(e0, b->stream);
+            last = batch_enqueue(b, t0, nsteps, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (last != FD_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                last = set_error(FD_ERR_CUDA, "fd_batch_autotune: timing");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / (double)nsteps;
+            if (per < bms) {
+                bms = per;
+                br = rows;
+                bs = stages;
+            }
+        }
+        if (last != FD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (last != FD_OK) return last;
+    if (br == 0) return set_error(FD_ERR_UNSUPPORTED, "fd_batch_autotune: no tiling fits");
+    s = batch_build(b, br, bs);
+    if (s != FD_OK) return s;
+    // the trial runs may have written the status word: report it now
+    FD_CUDA(cudaStreamSynchronize(b->stream), "fd_batch_autotune");
+    int status = 0;
+    FD_CUDA(cudaMemcpy(&status, b->status, sizeof status, cudaMemcpyDeviceToHost), "fd_batch_autotune: status");
+    if (status != 0) {
+        cudaMemset(b->status, 0, sizeof(int));
+        return set_error(FD_ERR_TIMEOUT, "fd_batch_autotune: a device wait gave up (code %d)", status);
+    }
+    if (best_rows) *best_rows = br;
+    if (best_stages) *best_stages = bs;
+    if (best_ms_per_step) *best_ms_per_step = bms;
+    return FD_OK;
 }
 
 extern "C" fd_status fd_batch_capture(fd_batch *b, int64_t t0, int64_t nt, double dt)

@@ -87,6 +87,8 @@ _SIGNATURES = [
     ("fd_batch_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(_vp)]),
     ("fd_batch_apply", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]),
+    ("fd_batch_autotune", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _c_f64p]),
     ("fd_batch_capture", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]),
     ("fd_batch_replay", ctypes.c_int, [_vp]),
     ("fd_batch_sync", ctypes.c_int, [_vp]),
@@ -330,6 +332,14 @@ def fd_batch_apply(b, t0, nt, dt):
     _check(lib().fd_batch_apply(b, int(t0), int(nt), float(dt)))
 
 
+def fd_batch_autotune(b, t0, nsteps, dt):
+    """Time candidate tilings of the batch and keep the fastest: (rows, stages, ms per step)."""
+    r, st, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib().fd_batch_autotune(b, int(t0), int(nsteps), float(dt), ctypes.byref(r), ctypes.byref(st),
+                                   ctypes.byref(ms)))
+    return r.value, st.value, ms.value
+
+
 def fd_batch_capture(b, t0, nt, dt):
     _check(lib().fd_batch_capture(b, int(t0), int(nt), float(dt)))
 
@@ -541,6 +551,11 @@ class Batch:
 
     def apply(self, t0, nt, dt):
         fd_batch_apply(self.handle, t0, nt, dt)
+
+    def autotune(self, t0, nsteps, dt):
+        """Pick the fastest tiling on the batch's own data: (rows, stages,
+        ms per step).  The trial runs advance the shots' fields."""
+        return fd_batch_autotune(self.handle, t0, nsteps, dt)
 
     def capture(self, t0, nt, dt):
         fd_batch_capture(self.handle, t0, nt, dt)

@@ -85,3 +85,37 @@ def test_batch_rejects_mismatched_operators():
     c = AcousticRun(shape, h, None, 8, m, eta, src, wav, rec, nt, flags=fd.FD_FLAG_REVERSE)
     with pytest.raises(fd.FDError):
         fd.Batch([a.op, c.op])
+
+
+def test_batch_autotune_picks_a_tiling_and_keeps_results_bitwise():
+    """fd_batch_autotune times tile heights x depths on the batch's own data
+    and keeps the fastest; the tiling changes no result bit, so after tuning
+    (and after forcing another tiling) the batch still reproduces the
+    individual runs exactly."""
+    nt = 40
+    shots = _shots(nt)
+    dt = shots[0][4]
+    alone = []
+    for sh in shots:
+        run = _make(sh, nt)
+        run.run(0, nt, dt)
+        alone.append((run.state(nt)[0], run.rec_trace()))
+    runs = [_make(sh, nt) for sh in shots]
+    batch = fd.Batch([r.op for r in runs], rows=32, stages=2)
+    rows, stages, ms = batch.autotune(0, 10, dt)
+    assert 10 <= rows <= 32 and 2 <= stages <= 4 and ms > 0
+    info = batch.info()
+    assert info[1] == stages and info[0] <= rows and info[2] > 0
+    for tiling in ("tuned", "forced"):
+        if tiling == "forced":
+            other = (10, 2) if (rows, stages) != (10, 2) else (16, 3)
+            batch = fd.Batch([r.op for r in runs], rows=other[0], stages=other[1])
+        for r in runs:
+            for s in r.u.slots:
+                s.zero_()
+            r.rec.data.zero_()
+        batch.apply(0, nt, dt)
+        batch.sync()
+        for run, (u_ref, rec_ref) in zip(runs, alone):
+            np.testing.assert_array_equal(run.state(nt)[0], u_ref)
+            np.testing.assert_array_equal(run.rec_trace(), rec_ref)

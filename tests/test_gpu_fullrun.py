@@ -11,13 +11,13 @@ Checked, element by element against the stored values:
   * the receiver traces rec[n][p] of a fixed, seeded subset of 512 of the
     10 201 receivers over all 1000 steps: relative L2 <= 1e-4 (the gate);
   * the final field u^1000 on every 8th node along each axis (64^3 nodes)
-    and its L2 norm over the whole grid, against the bound FP32 arithmetic
-    allows: the recurrence is stable (damping >= 0 only removes energy), so
-    its global error is at most the sum of the local rounding errors, each
-    step's at most k * 2^-24 relative with k = 3 (2M + 1) + 6 rounded
-    operations per point (the three axis sums, the centre term and the
-    update), i.e. nt * k * 2^-24: 2.0e-3 at SO8, 1.3e-3 at SO4, 3.4e-3 at
-    SO16.  (Measured: about 1e-4 at SO8, 4e-5 at SO4.)
+    and its L2 norm over the whole grid, against an FP32 error budget: the
+    recurrence is stable (damping >= 0 only removes energy), so its global
+    error grows about as the sum of the local rounding errors, each step's
+    at most k * 2^-24 relative with k = 3 (2M + 1) + 6 rounded operations
+    per point (the three axis sums, the centre term and the update), i.e.
+    nt * k * 2^-24: 2.0e-3 at SO8, 1.3e-3 at SO4, 3.4e-3 at SO16 (a budget,
+    not a proof; measured: about 1e-4 at SO8, 4e-5 at SO4).
 The stored values are the FP64 results rounded to FP32 (a relative change of
 at most 6e-8 per value, far below either tolerance).
 """
