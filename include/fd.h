@@ -368,7 +368,7 @@ fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stages);
  * columns x d0 chunks; all 0 when the operator runs the plain kernels). */
 fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, int *stages, int *ctas);
 
-/* Autotuner: time candidate tilings (tile heights 8..32 rows by prefetch
+/* Autotuner: time candidate tilings (tile heights 8..30 rows by prefetch
  * depths 2..4) over `nsteps` steps n = t0..t0+nsteps-1 with CUDA events on the
  * operator's stream and keep the fastest; writes the choice and its time per
  * step (ms) when the pointers are given.  The runs advance the operator's
@@ -409,7 +409,7 @@ fd_status fd_batch_create(fd_operator *const *ops, int nops, int rows, int stage
 fd_status fd_batch_apply(fd_batch *batch, int64_t t0, int64_t nt, double dt);
 /* Autotuner of the batch (the GPU analogue of the paper's block-size
  * auto-tuning, Automated code generation section): for tile heights of
- * 10..32 rows by prefetch depths 2..4, rebuilds the batch, runs steps
+ * 10..30 rows by prefetch depths 2..4, rebuilds the batch, runs steps
  * t0..t0+nsteps-1 of every shot timed with CUDA events on the operators'
  * stream (after up to 3 warm-up steps), and keeps the fastest; writes the
  * choice and its time per step (ms) when the pointers are given.  The runs

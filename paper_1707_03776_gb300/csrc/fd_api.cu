@@ -1094,7 +1094,7 @@ extern "C" fd_status fd_operator_autotune(fd_operator *op, int64_t t0, int64_t n
 {
     if (!op || nsteps < 1 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_operator_autotune: bad arguments");
     if (!op->tma.ready) return set_error(FD_ERR_UNSUPPORTED, "fd_operator_autotune: no tiled kernel to tune");
-    static const int kRows[] = {8, 10, 12, 14, 16, 18, 20, 24, 27, 32};
+    static const int kRows[] = {8, 10, 12, 14, 16, 18, 20, 24, 27, 30};
     cudaEvent_t e0, e1;
     FD_CUDA(cudaEventCreate(&e0), "fd_operator_autotune");
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1385,7 +1385,7 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int64_t t0, int64_t nsteps, 
     if (!b || nsteps < 1 || t0 < 0) return set_error(FD_ERR_INVALID_ARG, "fd_batch_autotune: bad arguments");
     fd_status s = batch_prepare(b, t0, nsteps, dt, "fd_batch_autotune");
     if (s != FD_OK) return s;
-    static const int kRows[] = {10, 12, 14, 16, 20, 24, 28, 32};
+    static const int kRows[] = {10, 12, 14, 16, 20, 24, 27, 30};
     cudaEvent_t e0, e1;
     FD_CUDA(cudaEventCreate(&e0), "fd_batch_autotune");
     if (cudaEventCreate(&e1) != cudaSuccess) {

@@ -37,7 +37,7 @@ namespace {
 using namespace tile_dev;
 
 template <int M, int P, bool IMG>
-__global__ void __launch_bounds__(16 * kMaxRows, 1)
+__global__ void __launch_bounds__(16 * kMaxRowsTiled + 32, 1)
     acoustic_tma_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_um,
                         const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_d,
                         float *__restrict__ out, const TileArgs a, const Coef cf, int *status,
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
         prefetch_map(&map_c);
         prefetch_map(&map_d);
     }
-    init_barriers<M, P>(sm);
+    init_barriers_ws<M, P>(sm, (blockDim.x >> 5) - 1);
     // CTA = (d0 chunk, tile column); chunks are balanced ranges of planes
     const int ncol = a.k1 * a.k2;
     const int tile = (int)(blockIdx.x % (unsigned)ncol);
@@ -70,9 +70,8 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
         if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
         return;
     }
-    unsigned it_u = 0, it_a = 0;
-    sweep_column<M, P, IMG>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc,
-                            src_row, sm, it_u, it_a, status, img);
+    sweep_column_ws<M, P, IMG>(&map_u, &map_um, &map_c, &map_d, out, a, cf, tile, z_lo, z_hi, src_tab + s0, nsrc,
+                               src_row, sm, status, img);
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -168,7 +167,7 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     auto occupancy = [&](int rows, int P) {
         const size_t per = tma_smem_bytes(M, P, rows, a.n0, 0) + 1024;
         int occ = (int)((size_t)smem_sm / per);
-        occ = std::min(occ, 2048 / (16 * rows));
+        occ = std::min(occ, 2048 / tma_threads(rows));
         return std::max(occ, 0);
     };
     // Choose the strip count k1 (tile height rows = ceil(n1/k1)): minimise the
@@ -206,7 +205,7 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     if (want_rows > 0) {
         const int k1 = (a.n1 + want_rows - 1) / want_rows;
         const int occ = occupancy((a.n1 + k1 - 1) / k1, kMinStages);
-        if (want_rows > kMaxRows || occ < 1)
+        if (want_rows > kMaxRowsTiled || occ < 1)
             return set_error(FD_ERR_UNSUPPORTED, "tiling: %d rows per tile do not fit", want_rows);
         best_k1 = k1;
         for (int kz = 1; kz <= kz_cap(k1, occ); kz++) {
@@ -217,7 +216,7 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
             }
         }
     } else {
-        for (int k1 = (a.n1 + kMaxRows - 1) / kMaxRows; k1 <= a.n1; k1++) {
+        for (int k1 = (a.n1 + kMaxRowsTiled - 1) / kMaxRowsTiled; k1 <= a.n1; k1++) {
             const int rows_max = (a.n1 + k1 - 1) / k1;
             const int occ = occupancy(rows_max, kMinStages);
             if (occ < 1) continue;
@@ -262,7 +261,7 @@ fd_status tma_plan_build(TmaPlan &plan, int kind, int space_order, const Geom &g
     plan.M = M;
     plan.stages = P;
     plan.args = a;
-    plan.threads = 16 * a.rows_max;
+    plan.threads = tma_threads(a.rows_max);
     plan.smem = tma_smem_bytes(M, P, a.rows_max, a.n0, 0);
     plan.smem_max = (size_t)smem_max;
     plan.src_cap = 0;

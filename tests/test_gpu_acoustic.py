@@ -236,7 +236,7 @@ def test_tilings_agree_bitwise_and_autotune():
     args = (cfg["shape"], cfg["spacing"], cfg["origin"], 8, cfg["m"], cfg["eta"], cfg["src_coords"],
             cfg["src_trace"], cfg["rec_coords"], cfg["nt"])
     results = []
-    for rows, stages in [(0, 0), (8, 2), (13, 3), (32, 4), (20, 2)]:
+    for rows, stages in [(0, 0), (8, 2), (13, 3), (30, 4), (20, 2)]:
         run = AcousticRun(*args)
         fd.fd_operator_set_tiling(run.op.handle, rows, stages)
         r, s, ctas = fd.fd_operator_get_tiling(run.op.handle)
@@ -253,7 +253,7 @@ def test_tilings_agree_bitwise_and_autotune():
         np.testing.assert_array_equal(rec, results[0][1])
     run = AcousticRun(*args)
     rows, stages, ms = fd.fd_operator_autotune(run.op.handle, 0, 5, cfg["dt"])
-    assert rows in (8, 10, 12, 14, 16, 18, 20, 24, 27, 32) and 2 <= stages <= 4 and ms > 0
+    assert rows in (8, 10, 12, 14, 16, 18, 20, 24, 27, 30) and 2 <= stages <= 4 and ms > 0
     with pytest.raises(fd.FDError) as e:
         fd.fd_operator_set_tiling(run.op.handle, 64, 2)
     assert e.value.status == fd.FD_ERR_UNSUPPORTED

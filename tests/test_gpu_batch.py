@@ -101,9 +101,9 @@ def test_batch_autotune_picks_a_tiling_and_keeps_results_bitwise():
         run.run(0, nt, dt)
         alone.append((run.state(nt)[0], run.rec_trace()))
     runs = [_make(sh, nt) for sh in shots]
-    batch = fd.Batch([r.op for r in runs], rows=32, stages=2)
+    batch = fd.Batch([r.op for r in runs], rows=30, stages=2)
     rows, stages, ms = batch.autotune(0, 10, dt)
-    assert 10 <= rows <= 32 and 2 <= stages <= 4 and ms > 0
+    assert 10 <= rows <= 30 and 2 <= stages <= 4 and ms > 0
     info = batch.info()
     assert info[1] == stages and info[0] <= rows and info[2] > 0
     for tiling in ("tuned", "forced"):
