@@ -540,7 +540,7 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
 // The sweep of one tile column with a producer warp (the single-grid tiled
 // kernel): the CTA's last warp issues the copies, P planes ahead, into ring
 // slots that the compute warps hand back through "empty" mbarriers (one
-// arrival per compute warp after its last read of the slot), so that a
+// arrival per compute thread after its last read of the slot), so that a
 // compute warp waits only for its own data, never for the other warps, and
 // warps may drift up to P planes apart.  Same arithmetic as sweep_column
 // (update_points).  Barriers: full u^n [NU], full aux [NA], empty u^n [NU],
@@ -554,7 +554,7 @@ __device__ inline void init_barriers_ws(const SweepSmem &sm, unsigned compute_wa
     constexpr int NU = M + 1 + P, NA = P + 1;
     if (threadIdx.x == 0) {
         for (int i = 0; i < NU + NA; i++) mbar_init(smem_addr(&sm.bars[i]), 1);
-        for (int i = NU + NA; i < 2 * (NU + NA); i++) mbar_init(smem_addr(&sm.bars[i]), compute_warps);
+        for (int i = NU + NA; i < 2 * (NU + NA); i++) mbar_init(smem_addr(&sm.bars[i]), 32 * compute_warps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *sm.abort = 0;
     }
@@ -740,13 +740,15 @@ __device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map
         if (!ok) break;
         // hand back the slots read for the last time: u^n plane j - M (the
         // centre just used) -- or plane j itself while j < M -- and the aux
-        // of output plane j - 2M
-        __syncwarp();
-        if (lane == 0) {
-            if (j < M) mbar_arrive_cta(BAR(kEmptyU + j % NU));
-            else if (j >= 2 * M) mbar_arrive_cta(BAR(kEmptyU + (j - M) % NU));
-            if (j >= 2 * M) mbar_arrive_cta(BAR(kEmptyA + (j - 2 * M) % NA));
-        }
+        // of output plane j - 2M.  Every thread fences its shared-memory
+        // reads (generic proxy) against the TMA copies (async proxy) that will
+        // refill the slots, then arrives: without the fence the refill could
+        // overtake reads still in flight (measured: results that differed
+        // from run to run whenever another kernel shared the SMs).
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (j < M) mbar_arrive_cta(BAR(kEmptyU + j % NU));
+        else if (j >= 2 * M) mbar_arrive_cta(BAR(kEmptyU + (j - M) % NU));
+        if (j >= 2 * M) mbar_arrive_cta(BAR(kEmptyA + (j - 2 * M) % NA));
         if (*abort_flag) break;
     }
     if (!ok && lane == 0) {
