@@ -432,6 +432,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         const bool wrote1 = j >= 2 * M && j < J1;
         if (wrote1) fence_proxy_async_global();  // u^{n+1} is read back through TMA
         if (!ok) *abort_flag = 1;
+        // the ring slots read above are refilled by TMA (async proxy) after
+        // this barrier: fence the generic-proxy reads against that
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (*abort_flag) {
             stop = true;

@@ -504,6 +504,9 @@ __device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um
             for (int k = 0; k < 4; k++) img_cur[k] = img_next[k];
         }
         if (!ok) *sm.abort = 1;
+        // the ring slots read above are refilled by TMA (async proxy) after
+        // this barrier: fence the generic-proxy reads against that
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (*sm.abort) {
             stop = true;
