@@ -17,7 +17,7 @@ Checked, element by element against the stored values:
     at most k * 2^-24 relative with k = 3 (2M + 1) + 6 rounded operations
     per point (the three axis sums, the centre term and the update), i.e.
     nt * k * 2^-24: 2.0e-3 at SO8, 1.3e-3 at SO4, 3.4e-3 at SO16 (a budget,
-    not a proof; measured: about 1e-4 at SO8, 4e-5 at SO4).
+    not a proof; measured: about 1e-4 at SO8 and SO16, 4e-5 at SO4).
 The stored values are the FP64 results rounded to FP32 (a relative change of
 at most 6e-8 per value, far below either tolerance).
 """
