@@ -663,6 +663,7 @@ def bench_learned(n=128, nt=2000):
         return out, time.perf_counter() - t0
 
     (net, data, hist), t_train = timed(lambda: closure.train_default(log_every=200))
+    n_samples = data.n
     cfg = wl.closure_config(n, nt, seed=1001, src="surface")
     fine = closure.FineReference(cfg)
     fine.run(20)
@@ -693,6 +694,23 @@ def bench_learned(n=128, nt=2000):
              "trace_rel_err_plain_coarse_SO4": closure.trace_error(op24.run(learned=False).cpu().numpy(), ref24),
              "trace_rel_err_learned": closure.trace_error(op24.run().cpu().numpy(), ref24)}
     del op24
+    # a closure that also sees where the coarse model misplaces interfaces
+    # (two sub-cell descriptors), trained on 8- and 24-cell sponges alike
+    del data
+    (net_d, data_d, hist_d), t_train_d = timed(
+        lambda: closure.train_default(n_coarse=96, nsub=2, sponge=(8, 24), log_every=200))
+    del data_d
+    errs_d = {}
+    for sp, c, r in ((8, cfg, ref), (24, cfg24, ref24)):
+        o = closure.ClosureOperator(c, net_d)
+        errs_d["sponge%d" % sp] = closure.trace_error(o.run().cpu().numpy(), r)
+        del o
+    thick["with_interface_descriptors"] = {
+        "nsub": 2, "train_models": "128 at 96^3 coarse, sponges 8 and 24 alternately", "train_s": t_train_d,
+        "loss_first_last": [hist_d[0][1], hist_d[-1][1]] if hist_d else None,
+        "trace_rel_err_learned_sponge8": errs_d["sponge8"], "trace_rel_err_learned_sponge24": errs_d["sponge24"]}
+    net_d.check()
+    del net_d
     # the network alone: CUDA events around its launches
     st = torch.cuda.current_stream()
     for _ in range(3):
@@ -733,7 +751,7 @@ def bench_learned(n=128, nt=2000):
             "trace_rel_err_learned": err, "trace_rel_err_plain_coarse": plain, "thick_sponge_check": thick,
             "s_learned": t_learned, "s_fine_grid": t_fine,
             "learned_vs_fine_time": t_learned / t_fine,
-            "train": {"s": t_train, "samples": data.n, "models": 128, "iters": 800, "rho": net.rho,
+            "train": {"s": t_train, "samples": n_samples, "models": 128, "iters": 800, "rho": net.rho,
                       "loss_first_last": [hist[0][1], hist[-1][1]]},
             "network_ms_per_step": ms_net, "network_share_of_learned_step": ms_net * nt / 1e3 / t_learned,
             "network_ms_per_step_mma_sync": ms_net_mma,

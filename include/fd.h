@@ -486,6 +486,14 @@ fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, const void *g
  * point's dense index (i0 n1 + i1) n2 + i2, divided by 2^24. */
 fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m, double scale,
                           double vref, double noise, uint64_t seed, void *x, void *cuda_stream);
+/* The same with nsub (0..5) per-node model descriptors s_k, FP32 slots of
+ * the grid's layout stored one after another from `sub` (k slots of n0
+ * planes each): channels 6 + 2k and 7 + 2k are (s_k u, s_k du) / scale, still
+ * linear in the wavefield.  The closure uses them for what the coarse grid's
+ * sampled m does not show: the model inside a coarse cell, and the damping. */
+fd_status fd_cnn_features_sub(const fd_grid *grid, const float *u, const float *u_prev, const float *m,
+                              const float *sub, int nsub, double scale, double vref, double noise, uint64_t seed,
+                              void *x, void *cuda_stream);
 /* Injection of a fine-grid field into a coarse grid whose nodes are every
  * factor-th fine node: coarse[i, j, k] = fine[f i, f j, f k]; the fine shape
  * must be factor * (n - 1) + 1 per axis (FD_ERR_INVALID_ARG otherwise).  Both

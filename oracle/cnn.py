@@ -113,13 +113,18 @@ def bf16_round(a):
     return r.astype(np.uint32).view(np.float32).reshape(a.shape)
 
 
-def features(u, u_prev, m, scale, vref):
-    """Closure inputs [n0, n1, n2, 6]: with du = u - u_prev and
-    q = 1/(m vref^2), (u, du, q u, q du, q^2 u, q^2 du) / scale."""
+def features(u, u_prev, m, scale, vref, sub=()):
+    """Closure inputs [n0, n1, n2, 6 + 2 len(sub)]: with du = u - u_prev and
+    q = 1/(m vref^2), (u, du, q u, q du, q^2 u, q^2 du) / scale, then for each
+    model descriptor s_k in `sub` (fields of u's shape) (s_k u, s_k du) / scale."""
     u = np.asarray(u, dtype=np.float64)
     du = u - np.asarray(u_prev, dtype=np.float64)
     q = 1.0 / (np.asarray(m, dtype=np.float64) * vref * vref)
-    return np.stack([u, du, q * u, q * du, q * q * u, q * q * du], axis=-1) / scale
+    ch = [u, du, q * u, q * du, q * q * u, q * q * du]
+    for s_k in sub:
+        s_k = np.asarray(s_k, dtype=np.float64)
+        ch += [s_k * u, s_k * du]
+    return np.stack(ch, axis=-1) / scale
 
 
 def splitmix64(key, counter):

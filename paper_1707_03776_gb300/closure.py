@@ -29,6 +29,14 @@ from . import fd
 
 CHANNELS = (6, 16, 16, 16, 1)
 NLAYER = len(CHANNELS) - 1
+# model descriptors a network built with nsub > 0 reads (workloads.closure_descriptors)
+MAX_SUB = 3
+
+
+def channels(nsub=0):
+    """Channel counts of the layers: 6 wavefield features plus 2 per model
+    descriptor in, then 16, 16, 16, 1."""
+    return (6 + 2 * int(nsub),) + CHANNELS[1:]
 # convolutions on the tcgen05 kernel (fd_cnn_conv3d_tc) unless a caller asks
 # for the mma.sync one (fd_cnn_conv3d); they agree to FP32 rounding
 TENSOR_MEMORY = True
@@ -46,18 +54,25 @@ def _frag_bytes(n):
 class ClosureNet:
     """FP32 master weights w[l] [27, cin, cout] (one flat buffer, so that one
     Adam launch updates all) and their packed BF16 tensor-core operands: frag
-    (forward) and frag_t (input gradient, taps mirrored) per layer."""
+    (forward) and frag_t (input gradient, taps mirrored) per layer.  With
+    nsub > 0 the first layer also reads (s_k u, s_k du) for the first nsub
+    model descriptors s_k."""
 
-    def __init__(self, seed=0, rho=1.0):
+    def __init__(self, seed=0, rho=1.0, nsub=0):
         import torch
         self.torch = torch
-        sizes = [27 * CHANNELS[i] * CHANNELS[i + 1] for i in range(NLAYER)]
+        if not 0 <= int(nsub) <= MAX_SUB:
+            raise ValueError("nsub must be in 0..%d" % MAX_SUB)
+        self.nsub = int(nsub)
+        self.channels = channels(nsub)
+        CH = self.channels
+        sizes = [27 * CH[i] * CH[i + 1] for i in range(NLAYER)]
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         n = int(self.offsets[-1])
         g = np.random.default_rng(seed)
         init = []
         for li in range(NLAYER):
-            cin = CHANNELS[li]
+            cin = CH[li]
             std = math.sqrt(2.0 / (27 * cin)) * (0.1 if li == NLAYER - 1 else 1.0)
             init.append(g.standard_normal(sizes[li]) * std)
         self.params = torch.from_numpy(np.concatenate(init).astype(np.float32)).cuda()
@@ -66,9 +81,9 @@ class ClosureNet:
         self.m2 = torch.zeros_like(self.params)
         self.adam_step = 0
         self.gb_dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
-        self.frag = [torch.zeros(_frag_bytes(CHANNELS[i + 1]), dtype=torch.uint8, device="cuda")
+        self.frag = [torch.zeros(_frag_bytes(CH[i + 1]), dtype=torch.uint8, device="cuda")
                      for i in range(NLAYER)]
-        self.frag_t = [torch.zeros(_frag_bytes(CHANNELS[i]), dtype=torch.uint8, device="cuda")
+        self.frag_t = [torch.zeros(_frag_bytes(CH[i]), dtype=torch.uint8, device="cuda")
                        for i in range(NLAYER)]
         # tcgen05 operand layout of the same weights, forward and mirrored
         self.frag_tc = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
@@ -80,16 +95,16 @@ class ClosureNet:
 
     def weight(self, li):
         a, b = int(self.offsets[li]), int(self.offsets[li + 1])
-        return self.params[a:b].view(27, CHANNELS[li], CHANNELS[li + 1])
+        return self.params[a:b].view(27, self.channels[li], self.channels[li + 1])
 
     def grad(self, li):
         a, b = int(self.offsets[li]), int(self.offsets[li + 1])
-        return self.grads[a:b].view(27, CHANNELS[li], CHANNELS[li + 1])
+        return self.grads[a:b].view(27, self.channels[li], self.channels[li + 1])
 
     def pack(self):
         st = _stream()
         for li in range(NLAYER):
-            cin, cout = CHANNELS[li], CHANNELS[li + 1]
+            cin, cout = self.channels[li], self.channels[li + 1]
             fd.fd_cnn_pack_weights(self.weight(li), cin, cout, 0, self.frag[li], st)
             fd.fd_cnn_pack_weights_tc(self.weight(li), cin, cout, 0, self.frag_tc[li], st)
             if li > 0:
@@ -135,6 +150,26 @@ class Workspace:
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
 
+def features(net, grid, u, u_prev, m, sub, scale, x, stream, noise=0.0, seed=0):
+    """The network's input features for grid states u, u_prev and model m;
+    `sub` holds the model descriptors (slots of the grid's layout one after
+    another) that a network with nsub > 0 reads."""
+    if net.nsub:
+        fd.fd_cnn_features_sub(grid, u, u_prev, m, sub, net.nsub, scale, net.vref, x, stream, noise=noise, seed=seed)
+    else:
+        fd.fd_cnn_features(grid, u, u_prev, m, scale, net.vref, x, stream, noise=noise, seed=seed)
+
+
+def descriptor_slots(grid, sub):
+    """Model descriptors [k, *shape] (numpy) copied into slots of the grid's
+    padded layout, one after another."""
+    import torch
+    sub = np.asarray(sub, dtype=np.float32)
+    out = torch.zeros((sub.shape[0],) + tuple(grid.padded_shape), dtype=torch.float32, device="cuda")
+    out[..., : sub.shape[-1]].copy_(torch.from_numpy(sub))
+    return out
+
+
 def network_forward(net, ws, stream=None, tensor_memory=None):
     """ws.h[0] (features) -> ws.out (FP32, one channel), on the tcgen05
     kernel (tensor_memory True, the default TENSOR_MEMORY) or the mma.sync
@@ -145,10 +180,10 @@ def network_forward(net, ws, stream=None, tensor_memory=None):
         last = li == NLAYER - 1
         y = ws.out if last else ws.h[li + 1]
         if tensor_memory:
-            fd.fd_cnn_conv3d_tc(ws.shape, ws.h[li], net.frag_tc[li], None, CHANNELS[li + 1], 0 if last else 1, None,
+            fd.fd_cnn_conv3d_tc(ws.shape, ws.h[li], net.frag_tc[li], None, net.channels[li + 1], 0 if last else 1, None,
                                 y, 1 if last else 0, net.tc_status, st)
         else:
-            fd.fd_cnn_conv3d(ws.shape, ws.h[li], net.frag[li], None, CHANNELS[li + 1], 0 if last else 1, None, y,
+            fd.fd_cnn_conv3d(ws.shape, ws.h[li], net.frag[li], None, net.channels[li + 1], 0 if last else 1, None, y,
                              1 if last else 0, st)
 
 
@@ -159,7 +194,7 @@ def network_backward(net, ws, stream=None, tensor_memory=None):
     tensor_memory = TENSOR_MEMORY if tensor_memory is None else tensor_memory
     cur = 0
     for li in range(NLAYER - 1, -1, -1):
-        cin, cout = CHANNELS[li], CHANNELS[li + 1]
+        cin, cout = net.channels[li], net.channels[li + 1]
         fd.fd_cnn_conv3d_wgrad(ws.shape, ws.h[li], ws.g[cur], cin, cout, net.grad(li), net.gb_dummy, st)
         if li > 0:
             # dL/dh_l = conv(g, flipped W_l) * (h_l > 0): h_l = relu(z_l)
@@ -194,6 +229,7 @@ class ClosureOperator:
         self.rec = fd.PointData("rec", self.grid, cfg["rec_coords"], self.nt)
         self.op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, c["space_order"], self.u, self.m, self.eta, src=self.src,
                               rec=self.rec, flags=flags)
+        self.sub = descriptor_slots(self.grid, c["sub"][: net.nsub]) if net.nsub else None
         self.ws = Workspace(self.shape)
 
     def run(self, nt=None, learned=True):
@@ -206,8 +242,8 @@ class ClosureOperator:
         g = self.grid.handle
         for n in range(nt):
             if learned:
-                fd.fd_cnn_features(g, self.u.slots[n % 2], self.u.slots[(n + 1) % 2], self.m.slots[0], 1.0,
-                                   self.net.vref, self.ws.h[0], st)
+                features(self.net, g, self.u.slots[n % 2], self.u.slots[(n + 1) % 2], self.m.slots[0], self.sub, 1.0,
+                         self.ws.h[0], st)
                 network_forward(self.net, self.ws, st)
             self.op.apply(n, 1, self.dt)
             if learned:
@@ -249,8 +285,8 @@ class FineReference:
 class Dataset:
     """Training samples of the closure: for coarse steps n of fine runs, the
     restricted fine states R u_f^{n-1}, R u_f^n, R u_f^{n+1}, the coarse step
-    S_c(R u_f^n, R u_f^{n-1}) ('base'), the coarse model m, and the sample's
-    feature scale s = RMS(R u_f^n)."""
+    S_c(R u_f^n, R u_f^{n-1}) ('base'), the coarse model m and its
+    descriptors, and the sample's feature scale s = RMS(R u_f^n)."""
 
     def __init__(self, cases, steps):
         import torch
@@ -265,6 +301,7 @@ class Dataset:
         ns = len(cases) * len(steps)
         self.states = torch.zeros((ns, 4) + ps, dtype=torch.float32, device="cuda")  # prev, cur, next, base
         self.models = torch.zeros((len(cases),) + ps, dtype=torch.float32, device="cuda")
+        self.subs = torch.zeros((len(cases), MAX_SUB) + ps, dtype=torch.float32, device="cuda")
         self.model_of = np.zeros(ns, dtype=np.int64)
         sumsq = torch.zeros(ns, dtype=torch.float32, device="cuda")
         st = _stream()
@@ -272,6 +309,7 @@ class Dataset:
         for mi, cfg in enumerate(cases):
             cs = cfg["coarse"]
             self.models[mi, ..., : self.shape[2]].copy_(torch.from_numpy(cs["m"]))
+            self.subs[mi, ..., : self.shape[2]].copy_(torch.from_numpy(cs["sub"][:MAX_SUB]))
             fine = FineReference(cfg, receivers=False)
             cm = fd.DenseData("m", self.cgrid)
             ce = fd.DenseData("eta", self.cgrid)
@@ -336,9 +374,9 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
         since += 1
         for k in g.integers(0, data.n, size=batch):
             s = float(data.scale[k])
-            mod = data.models[data.model_of[k]]
-            fd.fd_cnn_features(data.cgrid.handle, data.states[k, 1], data.states[k, 0], mod, s, net.vref, ws.h[0], st,
-                               noise=noise * s, seed=int(g.integers(0, 2 ** 63)))
+            mi = data.model_of[k]
+            features(net, data.cgrid.handle, data.states[k, 1], data.states[k, 0], data.models[mi], data.subs[mi], s,
+                     ws.h[0], st, noise=noise * s, seed=int(g.integers(0, 2 ** 63)))
             network_forward(net, ws, st)
             fd.fd_cnn_mse_grad(data.cgrid.handle, ws.out, data.states[k, 2], data.states[k, 3], s * net.rho, ws.g[0],
                                ws.loss, st)
@@ -353,16 +391,17 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
     return hist
 
 
-def train_default(count=128, n_coarse=64, nt=600, iters=800, seed=0, log_every=0):
+def train_default(count=128, n_coarse=64, nt=600, iters=800, seed=0, log_every=0, nsub=0, sponge=8):
     """The closure as trained for the evaluation workload: a dataset of
     `count` layered-model runs (workloads.closure_training_set), rho from the
     dataset, 800 Adam iterations of batch 4 with a cosine learning rate from
     2e-3 to 5e-5 (longer training lowered the one-step loss but not the
-    rollout error).  Returns (net, dataset, loss history)."""
+    rollout error); nsub model descriptors as extra inputs.  Returns (net,
+    dataset, loss history)."""
     from . import workloads as wl
-    cfgs, steps = wl.closure_training_set(count, n_coarse, nt)
+    cfgs, steps = wl.closure_training_set(count, n_coarse, nt, sponge=sponge)
     data = Dataset(cfgs, steps)
-    net = ClosureNet(seed=seed, rho=data.residual_ratio())
+    net = ClosureNet(seed=seed, rho=data.residual_ratio(), nsub=nsub)
     hist = train(net, data, iters, batch=4, lr=2e-3, lr_final=5e-5, seed=seed, log_every=log_every)
     return net, data, hist
 

@@ -312,11 +312,14 @@ __device__ __forceinline__ float unit_uniform(unsigned long long key, unsigned l
 
 // Closure input features, all linear in the wavefield: with du = u^n -
 // u^{n-1} and q = 1/(m vref^2) (the squared velocity relative to vref),
-// channels 0..5 = (u, du, q u, q du, q^2 u, q^2 du) / s; 6..15 = 0.  With
-// noise > 0, u^n and u^{n-1} first get noise * xi added, xi the unit-variance
-// deviates of counters 2p and 2p + 1 under key `seed` (training only).
+// channels 0..5 = (u, du, q u, q du, q^2 u, q^2 du) / s; with nsub model
+// descriptors s_k (fields of the grid's layout, sub + k * sub_stride),
+// channels 6 + 2k, 7 + 2k = (s_k u, s_k du) / s; the rest 0.  With noise > 0,
+// u^n and u^{n-1} first get noise * xi added, xi the unit-variance deviates of
+// counters 2p and 2p + 1 under key `seed` (training only).
 __global__ void features_kernel(Geom g, const float *__restrict__ u, const float *__restrict__ up,
-                                const float *__restrict__ m, float inv_scale, float inv_vref2, float noise,
+                                const float *__restrict__ m, const float *__restrict__ sub, int nsub,
+                                long long sub_stride, float inv_scale, float inv_vref2, float noise,
                                 unsigned long long seed, __nv_bfloat16 *__restrict__ x)
 {
     const long long total = g.n[0] * g.n[1] * g.n[2];
@@ -337,7 +340,11 @@ __global__ void features_kernel(Geom g, const float *__restrict__ u, const float
         dst[0] = __floats2bfloat162_rn(a, b);
         dst[1] = __floats2bfloat162_rn(q * a, q * b);
         dst[2] = __floats2bfloat162_rn(q * q * a, q * q * b);
-        for (int k = 3; k < kC / 2; k++) dst[k] = __floats2bfloat162_rn(0.f, 0.f);
+        for (int k = 0; k < nsub; k++) {
+            const float sk = sub[k * sub_stride + at];
+            dst[3 + k] = __floats2bfloat162_rn(sk * a, sk * b);
+        }
+        for (int k = 3 + nsub; k < kC / 2; k++) dst[k] = __floats2bfloat162_rn(0.f, 0.f);
     }
 }
 
@@ -532,20 +539,27 @@ extern "C" fd_status fd_cnn_conv3d_wgrad(const int64_t *shape, const void *x, co
     return FD_OK;
 }
 
-extern "C" fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m,
-                                     double scale, double vref, double noise, uint64_t seed, void *x, void *stream)
+extern "C" fd_status fd_cnn_features_sub(const fd_grid *grid, const float *u, const float *u_prev, const float *m,
+                                         const float *sub, int nsub, double scale, double vref, double noise,
+                                         uint64_t seed, void *x, void *stream)
 {
     if (!grid || grid->ndim != 3 || !u || !u_prev || !m || !x || !(scale > 0) || !(vref > 0) ||
-        !(noise >= 0))
+        !(noise >= 0) || nsub < 0 || nsub > 5 || (nsub > 0 && !sub))
         return set_error(FD_ERR_INVALID_ARG, "fd_cnn_features: bad arguments");
     if ((uintptr_t)x & 3) return set_error(FD_ERR_LAYOUT, "fd_cnn_features: x must be 4-byte aligned");
     const Geom g = geom3(grid);
     const long long total = g.n[0] * g.n[1] * g.n[2];
     features_kernel<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-        g, u, u_prev, m, (float)(1.0 / scale), (float)(1.0 / (vref * vref)), (float)noise,
-        (unsigned long long)seed, (__nv_bfloat16 *)x);
+        g, u, u_prev, m, sub, nsub, g.n[0] * g.s0, (float)(1.0 / scale), (float)(1.0 / (vref * vref)),
+        (float)noise, (unsigned long long)seed, (__nv_bfloat16 *)x);
     CNN_CUDA(cudaGetLastError(), "fd_cnn_features");
     return FD_OK;
+}
+
+extern "C" fd_status fd_cnn_features(const fd_grid *grid, const float *u, const float *u_prev, const float *m,
+                                     double scale, double vref, double noise, uint64_t seed, void *x, void *stream)
+{
+    return fd_cnn_features_sub(grid, u, u_prev, m, nullptr, 0, scale, vref, noise, seed, x, stream);
 }
 
 extern "C" fd_status fd_cnn_restrict(const fd_grid *fine_grid, const float *fine, const fd_grid *coarse_grid,

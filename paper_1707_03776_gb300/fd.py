@@ -102,6 +102,8 @@ _SIGNATURES = [
     ("fd_cnn_conv3d_tc", ctypes.c_int, [_c_i64p, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
                                         _vp, _vp]),
     ("fd_cnn_conv3d_wgrad", ctypes.c_int, [_c_i64p, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    ("fd_cnn_features_sub", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
     ("fd_cnn_features", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_uint64, _vp, _vp]),
     ("fd_cnn_restrict", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
@@ -418,6 +420,14 @@ def fd_cnn_conv3d_wgrad(shape, x, gy, cin, cout, gw, gb, stream=0):
 def fd_cnn_features(grid, u, u_prev, m, scale, vref, x, stream=0, noise=0.0, seed=0):
     _check(lib().fd_cnn_features(grid, _ptr(u), _ptr(u_prev), _ptr(m), float(scale), float(vref), float(noise),
                                  int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(x), int(stream) or None))
+
+
+def fd_cnn_features_sub(grid, u, u_prev, m, sub, nsub, scale, vref, x, stream=0, noise=0.0, seed=0):
+    """Closure features with nsub model descriptors (sub: nsub slots one after
+    another)."""
+    _check(lib().fd_cnn_features_sub(grid, _ptr(u), _ptr(u_prev), _ptr(m), _ptr(sub) if nsub else None, int(nsub),
+                                     float(scale), float(vref), float(noise), int(seed) & (2 ** 64 - 1), _ptr(x),
+                                     int(stream) or None))
 
 
 def fd_cnn_restrict(fine_grid, fine, coarse_grid, coarse, factor, sumsq=None, stream=0):

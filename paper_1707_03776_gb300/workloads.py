@@ -342,6 +342,7 @@ def closure_config(n_coarse=48, nt=400, seed=0, sponge=8, f0=8.0, vmin=1500.0, v
 
     src_c, trace_c = gaussian_source(hc, nt, dt_c)
     src_f, trace_f = gaussian_source(hf, 2 * nt, dt_f)
+    sub_c = closure_descriptors(v_c, v_f, eta_c, m_c, dt_c, vmax)
     side = np.arange(sponge + 1, nc - sponge - 1, 2, dtype=np.float64)
     if nrec_side is not None:
         side = side[:: max(1, side.size // int(nrec_side))][: int(nrec_side)]
@@ -350,20 +351,56 @@ def closure_config(n_coarse=48, nt=400, seed=0, sponge=8, f0=8.0, vmin=1500.0, v
     rec_coords = np.stack([X.ravel(), Y.ravel(), np.full(X.size, depth)], axis=1) * hc
     return dict(
         coarse=dict(shape=shape_c, spacing=sp_c, space_order=4, dt=dt_c, nt=nt, m=m_c, eta=eta_c,
-                    src_coords=src_c, src_trace=trace_c),
+                    src_coords=src_c, src_trace=trace_c, sub=sub_c),
         fine=dict(shape=shape_f, spacing=sp_f, space_order=16, dt=dt_f, nt=2 * nt, m=m_f, eta=eta_f,
                   src_coords=src_f, src_trace=trace_f),
         origin=(0.0, 0.0, 0.0), rec_coords=rec_coords, vmax=vmax, vmin=vmin, f0=f0, sponge=sponge, seed=seed,
         src_centre=centre)
 
 
-def closure_training_set(count=128, n_coarse=64, nt=600, f0=8.0, first=160, every=40):
+def closure_descriptors(v_c, v_f, eta_c, m_c, dt_c, vref):
+    """Per-coarse-node descriptors of what the coarse model cannot show (FP32,
+    [3, *coarse shape]), from the same model sampled on the fine grid whose
+    node 2i is coarse node i, in units of q = v^2 / vref^2:
+      0: the full-weighting average of q over the fine nodes of the coarse
+         cell (weights 1/4, 1/2, 1/4 per axis) minus q at the coarse node --
+         non-zero where an interface crosses the cell;
+      1: q(2i, 2j, 2k + 1) - q(2i, 2j, 2k - 1) on the fine grid -- which side
+         of the node the interface lies on along the depth axis;
+      2: dt sigma, the damping per coarse step (0 outside the sponge).
+    Fine indices outside the grid are clamped to its faces."""
+    q_f = (np.asarray(v_f, dtype=np.float64) / vref) ** 2
+    q_c = (np.asarray(v_c, dtype=np.float64) / vref) ** 2
+    nc = q_c.shape
+    nf = q_f.shape
+
+    def at(axis, off):
+        # fine index 2i + off along `axis`, clamped, for every coarse i
+        return np.clip(2 * np.arange(nc[axis]) + off, 0, nf[axis] - 1)
+
+    # the average minus q_c as the weighted sum of differences (weights sum
+    # to 1), so that it is exactly 0 where the fine nodes all equal q_c
+    dev = np.zeros(nc, dtype=np.float64)
+    wts = {-1: 0.25, 0: 0.5, 1: 0.25}
+    for o0, w0 in wts.items():
+        for o1, w1 in wts.items():
+            for o2, w2 in wts.items():
+                dev += w0 * w1 * w2 * (q_f[np.ix_(at(0, o0), at(1, o1), at(2, o2))] - q_c)
+    dz = q_f[np.ix_(at(0, 0), at(1, 0), at(2, 1))] - q_f[np.ix_(at(0, 0), at(1, 0), at(2, -1))]
+    damp = dt_c * np.asarray(eta_c, dtype=np.float64) / np.asarray(m_c, dtype=np.float64)
+    return np.stack([dev, dz, damp]).astype(np.float32)
+
+
+def closure_training_set(count=128, n_coarse=64, nt=600, f0=8.0, first=160, every=40, sponge=8):
     """The closure's training experiments: `count` seeded layered models
-    (seeds 0..count-1, random interior sources) on n_coarse^3 coarse grids,
-    and the coarse steps sampled from each fine run: every `every` steps from
-    `first` (after the 2/f0 s the source lasts, so that the network, which
-    does not see the source, learns the propagation error)."""
-    cfgs = [closure_config(n_coarse, nt, seed=s, f0=f0) for s in range(count)]
+    (seeds 0..count-1, random interior sources, `sponge`-cell sponges, or
+    with a sequence of widths model s gets width sponge[s % len]) on
+    n_coarse^3 coarse grids, and the coarse steps sampled from each fine run:
+    every `every` steps from `first` (after the 2/f0 s the source lasts, so
+    that the network, which does not see the source, learns the propagation
+    error)."""
+    widths = [int(sponge)] if np.ndim(sponge) == 0 else [int(w) for w in sponge]
+    cfgs = [closure_config(n_coarse, nt, seed=s, f0=f0, sponge=widths[s % len(widths)]) for s in range(count)]
     return cfgs, list(range(first, nt - 2, every))
 
 

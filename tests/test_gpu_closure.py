@@ -178,6 +178,18 @@ def test_features_restrict_correction_mse_adam():
     ref = cnn.features(nu, nup, mm, 2.0, 3000.0)
     got = x.float().cpu().numpy().reshape(shape + (16,))
     assert np.all(np.abs(got[..., :6] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max())
+    # with three model descriptors: channels 6..11, the rest zero
+    from paper_1707_03776_gb300 import workloads as wl
+    subs = [wl.random_field(shape, 60 + k) for k in range(3)]
+    sub = torch.zeros((3,) + grid.padded_shape, dtype=torch.float32, device="cuda")
+    for k in range(3):
+        sub[k, ..., : shape[2]].copy_(torch.from_numpy(subs[k]))
+    x.fill_(float("nan"))
+    fd.fd_cnn_features_sub(grid.handle, u.slots[0], u.slots[1], m.slots[0], sub, 3, 2.0, 3000.0, x, st)
+    ref = cnn.features(un, up, mm, 2.0, 3000.0, sub=subs)
+    got = x.float().cpu().numpy().reshape(shape + (16,))
+    assert np.all(np.abs(got[..., :12] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6 * np.abs(ref).max())
+    assert np.all(got[..., 12:] == 0.0)
 
     # restriction from a (2n-1)-node fine grid, with the sum of squares
     fshape = tuple(2 * s - 1 for s in shape)

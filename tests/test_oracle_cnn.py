@@ -122,6 +122,23 @@ def test_features_linear_and_reference_velocity():
     np.testing.assert_allclose(f2[..., 4], 48.0 * u, rtol=1e-13)
 
 
+def test_features_model_descriptors():
+    """Each descriptor s_k adds (s_k u, s_k du) / scale: a descriptor equal to
+    1 repeats channels 0 and 1, one equal to q repeats channels 2 and 3, and
+    without descriptors the six channels are unchanged."""
+    g = np.random.default_rng(13)
+    u, up = g.standard_normal((3, 4, 5)), g.standard_normal((3, 4, 5))
+    m = 1.0 / (1500.0 + 2000.0 * g.random((3, 4, 5))) ** 2
+    vref = 3500.0
+    q = 1.0 / (m * vref * vref)
+    f0 = cnn.features(u, up, m, 2.0, vref)
+    f = cnn.features(u, up, m, 2.0, vref, sub=[np.ones_like(u), q])
+    assert f.shape == (3, 4, 5, 10)
+    np.testing.assert_array_equal(f[..., :6], f0)
+    np.testing.assert_allclose(f[..., 6:8], f0[..., 0:2], rtol=1e-15)
+    np.testing.assert_allclose(f[..., 8:10], f0[..., 2:4], rtol=1e-14)
+
+
 def test_restrict_keeps_coinciding_nodes():
     fine = np.arange(9 * 7 * 5, dtype=np.float64).reshape(9, 7, 5)
     c = cnn.restrict(fine, 2)
