@@ -53,59 +53,126 @@ namespace {
 
 using namespace tile_dev;
 
+// True when a column of this shot fits the launch: its per-plane starts and
+// nsrc corners within the staged room.  Producer and compute warps decide it
+// alike, from the same values.
 template <int M, int P>
-__global__ void __launch_bounds__(16 * kMaxRows, 1)
+__device__ __forceinline__ bool column_fits(int rows_max, int src_cap, int n0, int nsrc)
+{
+    return nsrc <= src_cap && tma_smem_layout(M, P, rows_max, src_cap, n0).end <= (size_t)dynamic_smem_bytes();
+}
+
+// The persistent many-shot step.  Items (sorted by decreasing cost) are taken
+// from a global counter by the producer warp's lane as soon as the CTA's ring
+// has room: it publishes each item in one of two shared slots and, for a
+// tile column, issues the column's copies behind the previous column's, so
+// the pipeline does not drain between columns.  The compute warps take the
+// items in the same order: a column is swept by ws_consume_column (the
+// single-grid kernel's arithmetic), a receiver chunk interpolated.  Item
+// slot t % 2 carries the CTA's t-th item: "full" when the lane wrote it,
+// "empty" when every compute thread has read it.
+template <int M, int P>
+__global__ void __launch_bounds__(16 * kMaxRowsTiled + 32, 1)
     acoustic_batch_kernel(const ShotDesc *__restrict__ shots, const BatchItem *__restrict__ items, const int nitems,
                           int *next_item, const Coef cf, const int rows_max, const int src_cap, const long long n,
                           const int cur, int *status)
 {
     if (*reinterpret_cast<volatile int *>(status) != 0) return;
-    // everything but the per-plane starts (checked per shot below)
+    // everything but the per-plane starts (checked per column)
     if (!smem_fits<M, P>(rows_max, src_cap, 0, status)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SweepSmem sm = carve_smem<M, P>(smem_raw, rows_max, src_cap);
-    init_barriers<M, P>(sm);
-    unsigned it_u = 0, it_a = 0;
-    // items are sorted by decreasing cost; each CTA takes the next one as
-    // soon as it is free (longest processing time first, balanced at run time)
-    for (;;) {
-        if (threadIdx.x == 0) *sm.item = atomicAdd(next_item, 1);
-        __syncthreads();
-        const int k = *sm.item;
-        __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int compute_warps = (int)(blockDim.x >> 5) - 1;
+    const int nthreads = 32 * compute_warps;
+    init_barriers_ws<M, P>(sm, (unsigned)compute_warps);
+    constexpr int kItem = ws_item_bar<M, P>();
+    auto ITEM_FULL = [&](int s) { return smem_addr(&sm.bars[kItem + s]); };
+    auto ITEM_EMPTY = [&](int s) { return smem_addr(&sm.bars[kItem + 2 + s]); };
+    auto corners = [&](const ShotDesc *sd, int tile, int &s0) {
+        s0 = 0;
+        if (!sd->src) return 0;
+        s0 = sd->src_off[tile];
+        return sd->src_off[tile + 1] - s0;
+    };
+
+    if (warp == compute_warps) {
+        if (lane == 0) {
+            unsigned nu = 0, na = 0;
+            bool ok = true;
+            for (unsigned t = 0;; t++) {
+                const int k = atomicAdd(next_item, 1);
+                const int s = (int)(t & 1);
+                if (t >= 2 && !mbar_wait_flag(ITEM_EMPTY(s), ((t >> 1) - 1) & 1, sm.abort)) {
+                    ok = false;
+                    break;
+                }
+                sm.items[s] = k;
+                mbar_arrive_cta(ITEM_FULL(s));
+                if (k >= nitems) break;
+                const BatchItem it = items[k];
+                if (it.kind != 0) continue;
+                const ShotDesc *sd = shots + it.shot;
+                int s0;
+                if (!column_fits<M, P>(rows_max, src_cap, sd->a.n0, corners(sd, it.lo, s0))) {
+                    // more than the launch staged room for: nothing of this
+                    // column is issued
+                    atomicCAS(status, 0, (int)FD_ERR_LAYOUT);
+                    ok = false;
+                    break;
+                }
+                if (!ws_produce_column<M, P>(&sd->u_halo[cur], &sd->u_tile[cur ^ 1], &sd->c_tile, &sd->d_tile,
+                                             sd->a, it.lo, 0, sd->a.n0, sm, nu, na)) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok || *sm.abort) ws_drain<M, P>(sm, nu, na, status);
+        }
+        __syncwarp();
+        return;
+    }
+
+    // compute warps: every decision to leave is taken by all of them alike
+    // (named_barrier_or), so none waits at a barrier the others have left
+    unsigned ub = 0, ab = 0;
+    for (unsigned t = 0;; t++) {
+        const int s = (int)(t & 1);
+        const bool got = mbar_wait_flag(ITEM_FULL(s), (t >> 1) & 1, sm.abort);
+        const int k = got ? sm.items[s] : nitems;
+        if (got) mbar_arrive_cta(ITEM_EMPTY(s));
+        if (named_barrier_or(1, nthreads, !got)) {
+            if (threadIdx.x == 0) {
+                *sm.abort = 1;
+                atomicCAS(status, 0, (int)FD_ERR_TIMEOUT);
+            }
+            break;
+        }
         if (k >= nitems) break;
         const BatchItem it = items[k];
         const ShotDesc *sd = shots + it.shot;
         if (it.kind == 0) {
-            const TileArgs a = sd->a;
-            if (!smem_fits<M, P>(rows_max, src_cap, a.n0, status)) return;
-            const float *src_row = nullptr;
-            int s0 = 0, nsrc = 0;
-            if (sd->src) {
-                src_row = sd->src_trace + n * sd->src_stride;
-                s0 = sd->src_off[it.lo];
-                nsrc = sd->src_off[it.lo + 1] - s0;
-            }
-            if (nsrc > src_cap) {
-                // more corners than the launch staged room for (no copies
-                // are in flight between columns)
-                if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
-                return;
-            }
-            if (!sweep_column<M, P>(&sd->u_halo[cur], &sd->u_tile[cur ^ 1], &sd->c_tile, &sd->d_tile,
-                                    sd->slot[cur ^ 1], a, cf, it.lo, 0, a.n0, sd->src + s0, nsrc, src_row, sm, it_u,
-                                    it_a, status))
-                return;
+            int s0;
+            const int nsrc = corners(sd, it.lo, s0);
+            if (!column_fits<M, P>(rows_max, src_cap, sd->a.n0, nsrc)) break;  // the producer records it
+            const float *src_row = sd->src ? sd->src_trace + n * sd->src_stride : nullptr;
+            stage_sources(sd->src + s0, nsrc, sd->a.n0, sm, nthreads, [&] { named_barrier(1, nthreads); });
+            const bool ok = ws_consume_column<M, P, false>(sd->a, cf, it.lo, 0, sd->a.n0, sd->slot[cur ^ 1], nsrc,
+                                                           src_row, sm, ub, ab, status, ImagingArgs());
+            ub += (unsigned)(sd->a.n0 + 2 * M);
+            ab += (unsigned)sd->a.n0;
+            // also: every compute thread is done with this column's corners
+            if (named_barrier_or(1, nthreads, !ok || *sm.abort)) break;
         } else {
             // rec[n][p] = sum_k w_pk u^n(base_p + off_k), as interpolate_kernel
             const float *u = sd->slot[cur];
             float *row = sd->rec_trace + n * sd->rec_stride;
-            for (int p = it.lo + (int)threadIdx.x; p < it.hi; p += blockDim.x) {
+            for (int p = it.lo + (int)threadIdx.x; p < it.hi; p += nthreads) {
                 const int64_t b = sd->rec.base[p];
                 const float *w = sd->rec.weight + (int64_t)p * 8;
-                float s = 0.0f;
-                for (int c = 0; c < sd->rec.ncorner; c++) s = fmaf(w[c], u[b + sd->rec.corner_off[c]], s);
-                row[p] = s;
+                float acc = 0.0f;
+                for (int c = 0; c < sd->rec.ncorner; c++) acc = fmaf(w[c], u[b + sd->rec.corner_off[c]], acc);
+                row[p] = acc;
             }
         }
     }
@@ -113,18 +180,18 @@ __global__ void __launch_bounds__(16 * kMaxRows, 1)
 
 constexpr int kBatchRecChunk = 2048;
 
-template <int M>
-cudaError_t batch_configure(size_t smem)
+// The kernel instance of space order 2M with P stages (null: none).
+const void *batch_kernel(int M, int P)
 {
-    cudaError_t e = cudaFuncSetAttribute(acoustic_batch_kernel<M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(acoustic_batch_kernel<M, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(acoustic_batch_kernel<M, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-    return e;
+    switch (M * 8 + P) {
+#define CASE(MM, PP) \
+    case MM * 8 + PP: return reinterpret_cast<const void *>(&acoustic_batch_kernel<MM, PP>);
+#define CASES(MM) CASE(MM, 2) CASE(MM, 3) CASE(MM, 4)
+        CASES(1) CASES(2) CASES(3) CASES(4) CASES(5) CASES(6) CASES(7) CASES(8)
+#undef CASES
+#undef CASE
+    default: return nullptr;
+    }
 }
 
 }  // namespace
@@ -142,15 +209,22 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
         n0_max = std::max(n0_max, p->args.n0);
         if (p->has_src) src_cap = std::max(src_cap, p->src_cap);
     }
-    int dev = 0, sms = 0, smem_max = 0, smem_sm = 0;
+    int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const size_t smem = tma_smem_bytes(M, stages, rows_max, n0_max, src_cap);
     if (smem > (size_t)smem_max) return set_error(FD_ERR_UNSUPPORTED, "batch: %d stages do not fit", stages);
-    const int threads = 16 * rows_max;
-    int occ = std::min((int)((size_t)smem_sm / (smem + 1024)), 2048 / threads);
+    if (rows_max > kMaxRowsTiled)
+        return set_error(FD_ERR_UNSUPPORTED, "batch: tiles of %d rows (at most %d)", rows_max, kMaxRowsTiled);
+    const int threads = tma_threads(rows_max);
+    const void *kernel = batch_kernel(M, stages);
+    if (!kernel) return set_error(FD_ERR_UNSUPPORTED, "batch: space order %d, %d stages", 2 * M, stages);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    // resident CTAs per SM for these threads, registers and shared memory
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+    if (e != cudaSuccess) return set_error(FD_ERR_CUDA, "batch: kernel configuration: %s", cudaGetErrorString(e));
     if (occ < 1) return set_error(FD_ERR_UNSUPPORTED, "batch: tiles do not fit on an SM");
     const int nctas = sms * occ;
 
@@ -212,24 +286,13 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
     unsigned char *mem = nullptr;
     if (cudaMalloc((void **)&mem, b_shots + b_items + sizeof(int)) != cudaSuccess)
         return set_error(FD_ERR_NOMEM, "batch: device tables");
-    cudaError_t e = cudaMemcpyAsync(mem, shots.data(), b_shots, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(mem, shots.data(), b_shots, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !flat.empty())
         e = cudaMemcpyAsync(mem + b_shots, flat.data(), sizeof(BatchItem) * flat.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(mem);
         return set_error(FD_ERR_CUDA, "batch: upload: %s", cudaGetErrorString(e));
-    }
-    switch (M) {
-#define CASE(MM) \
-    case MM: e = batch_configure<MM>((size_t)smem_max); break;
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
-#undef CASE
-    default: e = cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) {
-        cudaFree(mem);
-        return set_error(FD_ERR_CUDA, "batch: kernel configuration: %s", cudaGetErrorString(e));
     }
     bp.M = M;
     bp.P = stages;

@@ -13,10 +13,10 @@
 //     centre values along d0 in a register queue, reads the d1/d2 neighbours
 //     of the plane M behind the newest from shared memory, adds the source
 //     injection of the corners it owns and writes u^{n+1} with 128-bit stores.
-// One elected thread issues the copies P planes ahead on mbarriers with
-// transaction counts; every wait is bounded by the global timer and, when it
-// gives up, the CTA records FD_ERR_TIMEOUT in the status word and leaves after
-// draining its own copies.
+// One lane of a producer warp issues the copies P planes ahead on mbarriers
+// with transaction counts, into slots the compute threads hand back; every
+// wait is bounded by the global timer and, when it gives up, the CTA records
+// FD_ERR_TIMEOUT in the status word and leaves after draining its own copies.
 #pragma once
 
 #include "fd_tma.h"
@@ -107,8 +107,8 @@ __host__ __device__ constexpr int round_up32(int x) { return (x + 31) / 32 * 32;
 __host__ __device__ inline int ring_plane_floats(int box_h) { return round_up32(box_h * kBoxW); }
 
 // Byte offsets of the areas of a tiled CTA's dynamic shared memory: the u^n
-// ring, the aux ring, the mbarriers, the abort flag and the batch kernel's
-// item slot (16 bytes), then src_cap
+// ring, the aux ring, the mbarriers, the abort flag and the batched kernel's
+// two work-item slots (16 bytes), then src_cap
 // injected corners of the tile and their n0 + 1 per-plane starts.  Both the
 // size a launch requests and the carve in the kernel come from here.
 struct SmemLayout {
@@ -121,7 +121,7 @@ __host__ __device__ inline SmemLayout tma_smem_layout(int M, int P, int rows_max
     SmemLayout l;
     l.aux = sizeof(float) * (size_t)NU * ring_plane_floats(rows_max + 2 * M);
     l.bars = l.aux + sizeof(float) * (size_t)NA * 3 * rows_max * kTileW;
-    l.abort = l.bars + sizeof(unsigned long long) * (size_t)(2 * (NU + NA));  // full and empty
+    l.abort = l.bars + sizeof(unsigned long long) * (size_t)(2 * (NU + NA) + 4);  // full, empty, items
     l.src = l.abort + 16;
     l.sstart = l.src + sizeof(SrcEntry) * (size_t)src_cap;
     l.end = l.sstart + sizeof(int) * (size_t)(n0 + 1);
@@ -144,9 +144,9 @@ __host__ __device__ inline size_t tma_smem_bytes(int M, int P, int rows_max, int
 struct SweepSmem {
     float *ring;                 // NU planes of plane_u floats
     float *aux;                  // NA slots of 3 boxes of plane_a floats
-    unsigned long long *bars;    // NU + NA mbarriers
+    unsigned long long *bars;    // 2 (NU + NA) + 4 mbarriers
     volatile int *abort;
-    int *item;                   // batch kernel: the work item being taken (next to abort)
+    volatile int *items;         // batched kernel: two work-item slots (after abort)
     SrcEntry *src;               // the column's injected corners
     int *sstart;                 // per-plane starts into src
     int plane_u, plane_a;
@@ -183,21 +183,10 @@ __device__ inline SweepSmem carve_smem(unsigned char *raw, int rows_max, int src
     sm.aux = reinterpret_cast<float *>(raw + l.aux);
     sm.bars = reinterpret_cast<unsigned long long *>(raw + l.bars);
     sm.abort = reinterpret_cast<volatile int *>(raw + l.abort);
-    sm.item = reinterpret_cast<int *>(raw + l.abort) + 1;
+    sm.items = reinterpret_cast<volatile int *>(raw + l.abort) + 2;
     sm.src = reinterpret_cast<SrcEntry *>(raw + l.src);
     sm.sstart = reinterpret_cast<int *>(raw + l.sstart);
     return sm;
-}
-
-template <int M, int P>
-__device__ inline void init_barriers(const SweepSmem &sm)
-{
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < M + 1 + P + P + 1; i++) mbar_init(smem_addr(&sm.bars[i]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *sm.abort = 0;
-    }
-    __syncthreads();
 }
 
 // One output plane of a thread's 4 consecutive d2 points (row r, columns
@@ -338,226 +327,39 @@ __device__ __forceinline__ void update_points(const float *__restrict__ pc, cons
         }
 }
 
-// Sweep output planes [z_lo, z_hi) of tile `tile` of one grid (the first 2M
-// iterations only load the u^n planes z_lo-M .. z_lo+M-1 that the first
-// output plane reads).  it_u / it_a count the u^n and aux loads this CTA has
-// consumed so far (ring slots and barrier phases continue across columns).
-// Returns false when a wait gave up (status set, copies drained).
-// With IMG, the imaging condition of `img` is accumulated at every point
-// written, from the value written (sources included).
-template <int M, int P, bool IMG = false>
-__device__ bool sweep_column(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
-                             const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
-                             int tile, int z_lo, int z_hi, const SrcEntry *__restrict__ src_tab, int nsrc,
-                             const float *__restrict__ src_row, const SweepSmem &sm, unsigned &it_u, unsigned &it_a,
-                             int *status, const ImagingArgs &img = ImagingArgs())
+// Column sweeps with a producer warp.  The CTA's last warp issues the
+// copies, P planes ahead, into ring slots that the compute warps hand back
+// through "empty" mbarriers (one arrival per compute thread after its last
+// read of the slot), so that a compute warp waits only for its own data,
+// never for the other warps, and warps may drift up to P planes apart.
+// Barriers: full u^n [NU], full aux [NA], empty u^n [NU], empty aux [NA],
+// then the batched kernel's work-item slots (full [2], empty [2]).  Every
+// wait is bounded; a wait that gives up records FD_ERR_TIMEOUT and raises
+// the CTA's abort flag, which every role checks; the producer then drains
+// the copies it still owes.
+//
+// Ring positions: the k-th u^n copy a CTA issues goes to slot k % NU and
+// completes phase (k / NU) & 1 of that slot's barriers, the k-th aux copy
+// likewise in slot k % NA.  A CTA that sweeps several columns (the batched
+// kernel) continues the count from one column to the next, so its pipeline
+// never drains between columns.
+template <int M, int P>
+__host__ __device__ constexpr int ws_item_bar()
 {
-    constexpr int NU = M + 1 + P;     // u^n planes alive: M behind the newest, the newest, P in flight
-    constexpr int NA = P + 1;         // aux planes (u^{n-1}, c, d)
-    constexpr int HV = (M + 3) / 4;   // float4 groups on each side of a thread's 4 points
-    constexpr int NR = 4 * (2 * HV + 1);
-    constexpr int Q = 2 * M + 1;      // d0 queue length
-
-    const int tid = threadIdx.x;
-    const int strip = tile / a.k2;
-    const int tile2 = tile - strip * a.k2;
-    const int row0 = (int)((long long)strip * a.n1 / a.k1);
-    const int rows = (int)((long long)(strip + 1) * a.n1 / a.k1) - row0;
-    const int col0 = tile2 * kTileW;
-    const int r = tid >> 4;
-    const int qc = tid & 15;
-    const bool active = r < rows && col0 + 4 * qc < a.n2;
-    const int J = (z_hi - z_lo) + 2 * M;
-    const int plane_u = sm.plane_u, plane_a = sm.plane_a;
-    float *ring = sm.ring;
-    float *aux = sm.aux;
-    unsigned long long *bars = sm.bars;
-    const uint32_t bytes_u = (uint32_t)(kBoxW * a.box_h * sizeof(float));
-    const uint32_t bytes_a = (uint32_t)(3 * a.rows_max * kTileW * sizeof(float));
-    const unsigned iu = it_u, ia = it_a;
-
-    // iteration j: u^n plane z_lo-M+j into ring slot (iu+j) % NU; for j >= 2M
-    // the aux of output plane z_lo+j-2M into aux slot (ia+j-2M) % NA
-    auto issue = [&](int j) {
-        const unsigned gu = iu + (unsigned)j;
-        const int su = (int)(gu % NU);
-        const uint32_t bu = smem_addr(&bars[su]);
-        mbar_expect_tx(bu, bytes_u);
-        // the stall hook arms the barrier but never issues the copy, so the
-        // wait for this plane runs out (the failure path under test)
-        if (a.stall_plane < 0 || tile != 0 || z_lo - M + j != a.stall_plane)
-            tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, z_lo - M + j, bu);
-        if (j >= 2 * M) {
-            const int ja = j - 2 * M;
-            const int sa = (int)((ia + (unsigned)ja) % NA);
-            const uint32_t ba = smem_addr(&bars[NU + sa]);
-            float *dst = aux + sa * 3 * plane_a;
-            mbar_expect_tx(ba, bytes_a);
-            tma_load_3d(smem_addr(dst), map_um, col0, row0, z_lo + ja, ba);
-            tma_load_3d(smem_addr(dst + plane_a), map_c, col0, row0, z_lo + ja, ba);
-            tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, z_lo + ja, ba);
-        }
-    };
-    auto wait_u = [&](int j) {
-        const unsigned gu = iu + (unsigned)j;
-        return mbar_wait_bounded(smem_addr(&bars[gu % NU]), (uint32_t)((gu / NU) & 1));
-    };
-    auto wait_a = [&](int ja) {
-        const unsigned ga = ia + (unsigned)ja;
-        return mbar_wait_bounded(smem_addr(&bars[NU + ga % NA]), (uint32_t)((ga / NA) & 1));
-    };
-
-    if (tid == 0)
-        for (int j = 0; j < P && j < J; j++) issue(j);
-
-    // the column's injected corners, staged in shared memory so that the
-    // plane loop never waits on them
-    SrcEntry *s_src = sm.src;
-    int *s_sstart = sm.sstart;
-    if (!src_row) nsrc = 0;
-    for (int q = tid; q < nsrc * 5; q += blockDim.x)
-        reinterpret_cast<int *>(s_src)[q] = reinterpret_cast<const int *>(src_tab)[q];
-    __syncthreads();
-    if (nsrc > 0) {
-        for (int z = tid; z <= a.n0; z += blockDim.x) {
-            int lo = 0, hi = nsrc;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_src[mid].z < z) lo = mid + 1; else hi = mid;
-            }
-            s_sstart[z] = lo;
-        }
-        __syncthreads();
-    }
-
-    // d0 queue: q[k] holds the thread's 4 centre values of plane z - M + k
-    // for the output plane z of the current iteration (shifted each plane)
-    float4 q[Q];
-#pragma unroll
-    for (int k = 0; k < Q; k++) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-    // imaging inputs (u0, u1, u2, grad) of the next output plane, loaded one
-    // iteration ahead into registers (up to M = 6; the highest orders load
-    // them when used), after an L2 prefetch three iterations ahead, so that
-    // their DRAM latency overlaps planes of work
-    constexpr bool kImgRegs = IMG && M <= 6;
-    float4 img_cur[4], img_next[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) img_cur[k] = img_next[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto img_fetch = [&](int zo_f, float4 (&dst)[4]) {
-        const long long at = (long long)zo_f * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
-        const float *src[4] = {img.u0, img.u1, img.u2, img.grad};
-        if (col0 + 4 * qc + 3 < a.n2) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) dst[k] = *reinterpret_cast<const float4 *>(src[k] + at);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < 4; i++)
-                    if (col0 + 4 * qc + i < a.n2) v[i] = src[k][at + i];
-                dst[k] = make_float4(v[0], v[1], v[2], v[3]);
-            }
-        }
-    };
-    auto img_prefetch_l2 = [&](int zo_f) {
-        const long long at = (long long)zo_f * a.s0 + (long long)(row0 + r) * a.s1 + col0 + 4 * qc;
-        const float *src[4] = {img.u0, img.u1, img.u2, img.grad};
-#pragma unroll
-        for (int k = 0; k < 4; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(src[k] + at));
-    };
-
-    int j = 0;
-    bool ok = true, stop = false;
-    // at high orders the d0 queue shift (2M+1 float4 moves per plane) is a
-    // large share of the instructions: unrolling two planes lets them be
-    // renamed instead (measured: SO12/16 about 5 % faster, SO8 1.4 % slower)
-#pragma unroll(M >= 6 ? 2 : 1)
-    for (; j < J; j++) {
-        if (tid == 0 && j + P < J) issue(j + P);
-        if constexpr (IMG) {
-            // output plane of the next iteration into registers, and the one
-            // two further into L2 (so that the register loads find it there)
-            const int zn = z_lo + j + 1 - 2 * M;
-            if (active && zn + 2 >= z_lo && zn + 2 < z_hi) img_prefetch_l2(zn + 2);
-            if (kImgRegs && active && zn >= z_lo && zn < z_hi) img_fetch(zn, img_next);
-        }
-        ok = wait_u(j) && ok;
-#pragma unroll
-        for (int k = 0; k < Q - 1; k++) q[k] = q[k + 1];
-        q[Q - 1] = *reinterpret_cast<const float4 *>(ring + ((iu + j) % NU) * plane_u + (r + M) * kBoxW + kSideHalo +
-                                                     4 * qc);
-        if (j >= 2 * M) {
-            const int ja = j - 2 * M;  // output plane z_lo + ja
-            const int zo = z_lo + ja;
-            ok = wait_a(ja) && ok;
-            if (ok && active) {
-                if constexpr (IMG && !kImgRegs) img_fetch(zo, img_cur);
-                update_points<M, IMG>(ring + ((iu + j - M) % NU) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc,
-                                      aux + ((ia + ja) % NA) * 3 * plane_a + r * kTileW + 4 * qc, plane_a, q, cf, a,
-                                      row0, col0, r, qc, zo, out, nsrc, s_src, s_sstart, src_row, img, img_cur);
-            }
-        }
-        if constexpr (kImgRegs) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) img_cur[k] = img_next[k];
-        }
-        if (!ok) *sm.abort = 1;
-        // the ring slots read above are refilled by TMA (async proxy) after
-        // this barrier: fence the generic-proxy reads against that
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (*sm.abort) {
-            stop = true;
-            break;
-        }
-    }
-
-    if (stop) {
-        // a wait gave up: record it, then drain this CTA's copies still in
-        // flight (issued up to min(j+P, J-1)) before leaving.  Every barrier
-        // is waited on, under one shared deadline, so that a copy that never
-        // lands does not stop the drain short of the ones behind it.
-        if (tid == 0) {
-            atomicExch(status, (int)FD_ERR_TIMEOUT);
-            const unsigned long long deadline = global_ns() + kWaitLimitNs;
-            const int last = (j + P < J) ? j + P : J - 1;
-            for (int i = j; i <= last; i++) {
-                const unsigned gu = iu + (unsigned)i;
-                mbar_wait_until(smem_addr(&bars[gu % NU]), (uint32_t)((gu / NU) & 1), deadline);
-                if (i >= 2 * M) {
-                    const unsigned ga = ia + (unsigned)(i - 2 * M);
-                    mbar_wait_until(smem_addr(&bars[NU + ga % NA]), (uint32_t)((ga / NA) & 1), deadline);
-                }
-            }
-        }
-        __syncthreads();
-        return false;
-    }
-    it_u = iu + (unsigned)J;
-    it_a = ia + (unsigned)(z_hi - z_lo);
-    return true;
+    return 2 * ((M + 1 + P) + (P + 1));
 }
 
-// The sweep of one tile column with a producer warp (the single-grid tiled
-// kernel): the CTA's last warp issues the copies, P planes ahead, into ring
-// slots that the compute warps hand back through "empty" mbarriers (one
-// arrival per compute thread after its last read of the slot), so that a
-// compute warp waits only for its own data, never for the other warps, and
-// warps may drift up to P planes apart.  Same arithmetic as sweep_column
-// (update_points).  Barriers: full u^n [NU], full aux [NA], empty u^n [NU],
-// empty aux [NA]; every wait is bounded, a wait that gives up records
-// FD_ERR_TIMEOUT and raises the CTA's abort flag, which every role checks;
-// the producer then drains the copies it still owes.  One column per CTA:
-// slots are not reused across columns.
 template <int M, int P>
 __device__ inline void init_barriers_ws(const SweepSmem &sm, unsigned compute_warps)
 {
-    constexpr int NU = M + 1 + P, NA = P + 1;
+    constexpr int NU = M + 1 + P, NA = P + 1, kItem = ws_item_bar<M, P>();
     if (threadIdx.x == 0) {
         for (int i = 0; i < NU + NA; i++) mbar_init(smem_addr(&sm.bars[i]), 1);
         for (int i = NU + NA; i < 2 * (NU + NA); i++) mbar_init(smem_addr(&sm.bars[i]), 32 * compute_warps);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(smem_addr(&sm.bars[kItem + i]), 1);
+            mbar_init(smem_addr(&sm.bars[kItem + 2 + i]), 32 * compute_warps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *sm.abort = 0;
     }
@@ -577,21 +379,135 @@ __device__ __forceinline__ bool mbar_wait_flag(uint32_t bar, uint32_t parity, vo
     return true;
 }
 
-template <int M, int P, bool IMG = false>
-__device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
-                                const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
-                                int tile, int z_lo, int z_hi, const SrcEntry *__restrict__ src_tab, int nsrc,
-                                const float *__restrict__ src_row, const SweepSmem &sm, int *status,
-                                const ImagingArgs &img = ImagingArgs())
+// Barrier `id` over the first `nthreads` threads (the compute warps),
+// returning whether any of them passed v = true: a decision all of them take
+// alike.  Not the .aligned form: threads may arrive from divergent paths.
+__device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "barrier.cta.red.or.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Stage a column's injected corners and their per-plane starts (planes
+// 0..n0) in shared memory, by threads [0, nthreads), `sync` after each part.
+template <class Sync>
+__device__ inline void stage_sources(const SrcEntry *__restrict__ src_tab, int nsrc, int n0, const SweepSmem &sm,
+                                     int nthreads, Sync sync)
+{
+    const int tid = threadIdx.x;
+    for (int q = tid; q < nsrc * 5; q += nthreads)
+        reinterpret_cast<int *>(sm.src)[q] = reinterpret_cast<const int *>(src_tab)[q];
+    sync();
+    if (nsrc > 0) {
+        for (int z = tid; z <= n0; z += nthreads) {
+            int lo = 0, hi = nsrc;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sm.src[mid].z < z) lo = mid + 1; else hi = mid;
+            }
+            sm.sstart[z] = lo;
+        }
+        sync();
+    }
+}
+
+// The producer's part of the sweep of output planes [z_lo, z_hi) of tile
+// `tile` (one lane): u^n plane j of the column (z = z_lo - M + j) is the
+// CTA's u^n copy nu + j, the aux of output plane ja its aux copy na + ja; nu
+// and na advance by the copies issued.  False when a wait gave up or the
+// abort flag is up (the caller then drains).
+template <int M, int P>
+__device__ bool ws_produce_column(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
+                                  const CUtensorMap *map_d, const TileArgs &a, int tile, int z_lo, int z_hi,
+                                  const SweepSmem &sm, unsigned &nu, unsigned &na)
+{
+    constexpr int NU = M + 1 + P, NA = P + 1;
+    constexpr int kFullA = NU, kEmptyU = NU + NA, kEmptyA = 2 * NU + NA;
+    const int strip = tile / a.k2;
+    const int row0 = (int)((long long)strip * a.n1 / a.k1);
+    const int col0 = (tile - strip * a.k2) * kTileW;
+    const int J = (z_hi - z_lo) + 2 * M;
+    const uint32_t bytes_u = (uint32_t)(kBoxW * a.box_h * sizeof(float));
+    const uint32_t bytes_a = (uint32_t)(3 * a.rows_max * kTileW * sizeof(float));
+    auto BAR = [&](int i) { return smem_addr(&sm.bars[i]); };
+    for (int j = 0; j < J; j++) {
+        const unsigned U = nu;
+        const int su = (int)(U % NU);
+        // the slot's previous copy, U - NU, must have been handed back
+        if (U >= NU && !mbar_wait_flag(BAR(kEmptyU + su), ((U / NU) - 1) & 1, sm.abort)) return false;
+        mbar_expect_tx(BAR(su), bytes_u);
+        // the stall hook arms the barrier but never issues the copy, so the
+        // wait for this plane runs out (the failure path under test)
+        if (a.stall_plane < 0 || tile != 0 || z_lo - M + j != a.stall_plane)
+            tma_load_3d(smem_addr(sm.ring + su * sm.plane_u), map_u, col0 - kSideHalo, row0 - M, z_lo - M + j,
+                        BAR(su));
+        nu = U + 1;
+        if (j >= 2 * M) {
+            const unsigned A = na;
+            const int sa = (int)(A % NA);
+            if (A >= NA && !mbar_wait_flag(BAR(kEmptyA + sa), ((A / NA) - 1) & 1, sm.abort)) return false;
+            float *dst = sm.aux + sa * 3 * sm.plane_a;
+            const int z = z_lo + (j - 2 * M);
+            mbar_expect_tx(BAR(kFullA + sa), bytes_a);
+            tma_load_3d(smem_addr(dst), map_um, col0, row0, z, BAR(kFullA + sa));
+            tma_load_3d(smem_addr(dst + sm.plane_a), map_c, col0, row0, z, BAR(kFullA + sa));
+            tma_load_3d(smem_addr(dst + 2 * sm.plane_a), map_d, col0, row0, z, BAR(kFullA + sa));
+            na = A + 1;
+        }
+    }
+    return !*sm.abort;
+}
+
+// After a failed wait: raise the abort flag, record FD_ERR_TIMEOUT (unless an
+// error is already recorded) and wait, under one shared deadline, for the
+// copies possibly still in flight (the last NU u^n and NA aux copies).
+template <int M, int P>
+__device__ void ws_drain(const SweepSmem &sm, unsigned nu, unsigned na, int *status)
+{
+    constexpr int NU = M + 1 + P, NA = P + 1;
+    *sm.abort = 1;
+    atomicCAS(status, 0, (int)FD_ERR_TIMEOUT);
+    const unsigned long long deadline = global_ns() + kWaitLimitNs;
+    for (unsigned k = nu > NU ? nu - NU : 0; k < nu; k++)
+        mbar_wait_until(smem_addr(&sm.bars[k % NU]), (k / NU) & 1, deadline);
+    for (unsigned k = na > NA ? na - NA : 0; k < na; k++)
+        mbar_wait_until(smem_addr(&sm.bars[NU + k % NA]), (k / NA) & 1, deadline);
+}
+
+// The compute warps' part of the same sweep: u^n plane j of the column is
+// the CTA's copy ub + j, the aux of output plane ja its aux copy ab + ja (as
+// the producer issued them).  Each thread hands every slot back after its
+// last read of it: planes j < M and j >= J - M right after they enter the d0
+// queue, every other plane after it served as the centre plane (iteration
+// j + M), the aux of output plane ja at iteration ja + 2M.  False when a wait
+// gave up (FD_ERR_TIMEOUT recorded, abort flag raised) or the flag was up.
+// With IMG, the imaging condition of `img` is accumulated at every point
+// written, from the value written (sources included).
+template <int M, int P, bool IMG>
+__device__ bool ws_consume_column(const TileArgs &a, const Coef &cf, int tile, int z_lo, int z_hi,
+                                  float *__restrict__ out, int nsrc, const float *__restrict__ src_row,
+                                  const SweepSmem &sm, unsigned ub, unsigned ab, int *status,
+                                  const ImagingArgs &img)
 {
     constexpr int NU = M + 1 + P;     // u^n planes alive: M behind the newest, the newest, P in flight
     constexpr int NA = P + 1;         // aux planes (u^{n-1}, c, d)
-    constexpr int Q = 2 * M + 1;      // d0 queue length
     constexpr int kFullA = NU, kEmptyU = NU + NA, kEmptyA = 2 * NU + NA;
 
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int compute_warps = (int)(blockDim.x >> 5) - 1;
+    const int lane = tid & 31;
     const int strip = tile / a.k2;
     const int tile2 = tile - strip * a.k2;
     const int row0 = (int)((long long)strip * a.n1 / a.k1);
@@ -601,86 +517,11 @@ __device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map
     const int qc = tid & 15;
     const int J = (z_hi - z_lo) + 2 * M;
     const int plane_u = sm.plane_u, plane_a = sm.plane_a;
-    float *ring = sm.ring;
-    float *aux = sm.aux;
-    unsigned long long *bars = sm.bars;
+    const float *ring = sm.ring;
+    const float *aux = sm.aux;
     volatile int *abort_flag = sm.abort;
-    auto BAR = [&](int i) { return smem_addr(&bars[i]); };
+    auto BAR = [&](int i) { return smem_addr(&sm.bars[i]); };
 
-    // the column's injected corners, staged in shared memory (all threads)
-    SrcEntry *s_src = sm.src;
-    int *s_sstart = sm.sstart;
-    if (!src_row) nsrc = 0;
-    for (int q = tid; q < nsrc * 5; q += blockDim.x)
-        reinterpret_cast<int *>(s_src)[q] = reinterpret_cast<const int *>(src_tab)[q];
-    __syncthreads();
-    if (nsrc > 0) {
-        for (int z = tid; z <= a.n0; z += blockDim.x) {
-            int lo = 0, hi = nsrc;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_src[mid].z < z) lo = mid + 1; else hi = mid;
-            }
-            s_sstart[z] = lo;
-        }
-        __syncthreads();
-    }
-
-    if (warp == compute_warps) {
-        // producer: sweep plane j of u^n into slot j % NU; for j >= 2M the
-        // aux of output plane j - 2M into slot (j - 2M) % NA
-        if (lane == 0) {
-            const uint32_t bytes_u = (uint32_t)(kBoxW * a.box_h * sizeof(float));
-            const uint32_t bytes_a = (uint32_t)(3 * a.rows_max * kTileW * sizeof(float));
-            int ju = 0, jaux = 0;  // u planes / aux planes issued
-            bool ok = true;
-            for (int j = 0; j < J && ok; j++) {
-                const int su = j % NU;
-                // the slot's previous plane j - NU was last read at iteration
-                // j - NU + M (as the centre plane) or j - NU (if j - NU < M)
-                if (j >= NU && !mbar_wait_flag(BAR(kEmptyU + su), (uint32_t)(((j / NU) - 1) & 1), abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                mbar_expect_tx(BAR(su), bytes_u);
-                // the stall hook arms the barrier but never issues the copy,
-                // so the wait for this plane runs out (the failure path under test)
-                if (a.stall_plane < 0 || tile != 0 || z_lo - M + j != a.stall_plane)
-                    tma_load_3d(smem_addr(ring + su * plane_u), map_u, col0 - kSideHalo, row0 - M, z_lo - M + j,
-                                BAR(su));
-                ju++;
-                if (j >= 2 * M) {
-                    const int ja = j - 2 * M;
-                    const int sa = ja % NA;
-                    if (ja >= NA && !mbar_wait_flag(BAR(kEmptyA + sa), (uint32_t)(((ja / NA) - 1) & 1), abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    float *dst = aux + sa * 3 * plane_a;
-                    mbar_expect_tx(BAR(kFullA + sa), bytes_a);
-                    tma_load_3d(smem_addr(dst), map_um, col0, row0, z_lo + ja, BAR(kFullA + sa));
-                    tma_load_3d(smem_addr(dst + plane_a), map_c, col0, row0, z_lo + ja, BAR(kFullA + sa));
-                    tma_load_3d(smem_addr(dst + 2 * plane_a), map_d, col0, row0, z_lo + ja, BAR(kFullA + sa));
-                    jaux++;
-                }
-            }
-            if (!ok || *abort_flag) {
-                // drain the copies possibly still in flight (the last of each
-                // ring), under one shared deadline
-                *abort_flag = 1;
-                atomicExch(status, (int)FD_ERR_TIMEOUT);
-                const unsigned long long deadline = global_ns() + kWaitLimitNs;
-                for (int k = ju > NU ? ju - NU : 0; k < ju; k++)
-                    mbar_wait_until(BAR(k % NU), (uint32_t)((k / NU) & 1), deadline);
-                for (int k = jaux > NA ? jaux - NA : 0; k < jaux; k++)
-                    mbar_wait_until(BAR(kFullA + k % NA), (uint32_t)((k / NA) & 1), deadline);
-            }
-        }
-        __syncwarp();
-        return;
-    }
-
-    // compute warps
     const bool active = r < rows && col0 + 4 * qc < a.n2;
     constexpr bool kImgRegs = IMG && M <= 6;
     float4 img_cur[4], img_next[4];
@@ -710,6 +551,7 @@ __device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map
         for (int k = 0; k < 4; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(src[k] + at));
     };
 
+    constexpr int Q = 2 * M + 1;  // d0 queue length
     float4 q[Q];
 #pragma unroll
     for (int k = 0; k < Q; k++) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -721,19 +563,21 @@ __device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map
             if (active && zn + 2 >= z_lo && zn + 2 < z_hi) img_prefetch_l2(zn + 2);
             if (kImgRegs && active && zn >= z_lo && zn < z_hi) img_fetch(zn, img_next);
         }
-        ok = mbar_wait_flag(BAR(j % NU), (uint32_t)((j / NU) & 1), abort_flag);
+        const unsigned U = ub + (unsigned)j;
+        ok = mbar_wait_flag(BAR((int)(U % NU)), (U / NU) & 1, abort_flag);
 #pragma unroll
         for (int k = 0; k < Q - 1; k++) q[k] = q[k + 1];
-        q[Q - 1] = *reinterpret_cast<const float4 *>(ring + (j % NU) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc);
+        q[Q - 1] = *reinterpret_cast<const float4 *>(ring + (U % NU) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc);
         if (ok && j >= 2 * M) {
             const int ja = j - 2 * M;  // output plane z_lo + ja
             const int zo = z_lo + ja;
-            ok = mbar_wait_flag(BAR(kFullA + ja % NA), (uint32_t)((ja / NA) & 1), abort_flag);
+            const unsigned A = ab + (unsigned)ja;
+            ok = mbar_wait_flag(BAR(kFullA + (int)(A % NA)), (A / NA) & 1, abort_flag);
             if (ok && active) {
                 if constexpr (IMG && !kImgRegs) img_fetch(zo, img_cur);
-                update_points<M, IMG>(ring + ((j - M) % NU) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc,
-                                      aux + (ja % NA) * 3 * plane_a + r * kTileW + 4 * qc, plane_a, q, cf, a,
-                                      row0, col0, r, qc, zo, out, nsrc, s_src, s_sstart, src_row, img, img_cur);
+                update_points<M, IMG>(ring + ((U - M) % NU) * plane_u + (r + M) * kBoxW + kSideHalo + 4 * qc,
+                                      aux + (A % NA) * 3 * plane_a + r * kTileW + 4 * qc, plane_a, q, cf, a,
+                                      row0, col0, r, qc, zo, out, nsrc, sm.src, sm.sstart, src_row, img, img_cur);
             }
         }
         if constexpr (kImgRegs) {
@@ -741,23 +585,53 @@ __device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map
             for (int k = 0; k < 4; k++) img_cur[k] = img_next[k];
         }
         if (!ok) break;
-        // hand back the slots read for the last time: u^n plane j - M (the
-        // centre just used) -- or plane j itself while j < M -- and the aux
-        // of output plane j - 2M.  Every thread fences its shared-memory
-        // reads (generic proxy) against the TMA copies (async proxy) that will
-        // refill the slots, then arrives: without the fence the refill could
-        // overtake reads still in flight (measured: results that differed
-        // from run to run whenever another kernel shared the SMs).
+        // Every thread fences its shared-memory reads (generic proxy) against
+        // the TMA copies (async proxy) that will refill the slots, then
+        // hands them back: without the fence a refill could overtake reads
+        // still in flight (measured: results that differed from run to run
+        // whenever another kernel shared the SMs).
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (j < M) mbar_arrive_cta(BAR(kEmptyU + j % NU));
-        else if (j >= 2 * M) mbar_arrive_cta(BAR(kEmptyU + (j - M) % NU));
-        if (j >= 2 * M) mbar_arrive_cta(BAR(kEmptyA + (j - 2 * M) % NA));
-        if (*abort_flag) break;
+        if (j < M || j >= J - M) mbar_arrive_cta(BAR(kEmptyU + (int)(U % NU)));
+        if (j >= 2 * M) {
+            mbar_arrive_cta(BAR(kEmptyU + (int)((U - M) % NU)));
+            mbar_arrive_cta(BAR(kEmptyA + (int)((ab + (unsigned)(j - 2 * M)) % NA)));
+        }
+        if (*abort_flag) {
+            ok = false;
+            break;
+        }
     }
     if (!ok && lane == 0) {
         *abort_flag = 1;
-        atomicExch(status, (int)FD_ERR_TIMEOUT);
+        atomicCAS(status, 0, (int)FD_ERR_TIMEOUT);
     }
+    return ok;
+}
+
+// One tile column per CTA (the single-grid kernel): stage the column's
+// corners (every thread), then the last warp produces and the others
+// compute.
+template <int M, int P, bool IMG = false>
+__device__ void sweep_column_ws(const CUtensorMap *map_u, const CUtensorMap *map_um, const CUtensorMap *map_c,
+                                const CUtensorMap *map_d, float *__restrict__ out, const TileArgs &a, const Coef &cf,
+                                int tile, int z_lo, int z_hi, const SrcEntry *__restrict__ src_tab, int nsrc,
+                                const float *__restrict__ src_row, const SweepSmem &sm, int *status,
+                                const ImagingArgs &img = ImagingArgs())
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int compute_warps = (int)(blockDim.x >> 5) - 1;
+    if (!src_row) nsrc = 0;
+    stage_sources(src_tab, nsrc, a.n0, sm, (int)blockDim.x, [] { __syncthreads(); });
+    if (warp == compute_warps) {
+        if (lane == 0) {
+            unsigned nu = 0, na = 0;
+            if (!ws_produce_column<M, P>(map_u, map_um, map_c, map_d, a, tile, z_lo, z_hi, sm, nu, na))
+                ws_drain<M, P>(sm, nu, na, status);
+        }
+        __syncwarp();
+        return;
+    }
+    ws_consume_column<M, P, IMG>(a, cf, tile, z_lo, z_hi, out, nsrc, src_row, sm, 0u, 0u, status, img);
 }
 
 }  // namespace tile_dev

@@ -119,3 +119,41 @@ def test_batch_autotune_picks_a_tiling_and_keeps_results_bitwise():
         for run, (u_ref, rec_ref) in zip(runs, alone):
             np.testing.assert_array_equal(run.state(nt)[0], u_ref)
             np.testing.assert_array_equal(run.rec_trace(), rec_ref)
+
+
+@pytest.mark.parametrize("so,rows,stages", [(4, 12, 3), (16, 10, 2)])
+def test_batch_sweeps_several_columns_per_cta(so, rows, stages):
+    """More tile columns than CTAs, so that each persistent CTA sweeps two or
+    three columns in a row with its ring positions running on from one column
+    to the next (the producer warp fetches the next column while the compute
+    warps finish the last): fields and traces still equal the individual runs
+    bit for bit, at a low and the highest space order."""
+    nt = 24
+    h = (10.0,) * 3
+    dt = 0.3 * 10.0 / 4500.0
+    shots = []
+    for i, shape in enumerate([(48, 144, 320), (40, 150, 300), (56, 130, 256)] * 6):
+        v = wl.random_smooth_velocity(shape, 40 + i, sigma_cells=4.0, vmin=1500.0, vmax=4500.0)
+        m = (1.0 / v ** 2).astype(np.float32)
+        eta = (m.astype(np.float64) * wl.sponge_sigma(shape, h, 6, 4500.0, ref_width=40)).astype(np.float32)
+        src = np.array([[shape[0] * 5.0, shape[1] * 5.0, 60.0 + 10.0 * i]])
+        gx = np.linspace(60.0, (shape[0] - 7) * 10.0, 5)
+        rec = np.stack([gx, np.full(5, shape[1] * 5.0), np.full(5, 75.0)], axis=1)
+        wav = wl.ricker(nt, dt, 25.0).astype(np.float32).reshape(nt, 1)
+        shots.append((shape, m, eta, src, wav, rec))
+    alone = []
+    for shape, m, eta, src, wav, rec in shots:
+        run = AcousticRun(shape, h, None, so, m, eta, src, wav, rec, nt)
+        run.run(0, nt, dt)
+        alone.append((run.state(nt)[0], run.rec_trace()))
+        del run
+    runs = [AcousticRun(shape, h, None, so, m, eta, src, wav, rec, nt) for shape, m, eta, src, wav, rec in shots]
+    batch = fd.Batch([r.op for r in runs], rows=rows, stages=stages)
+    r_used, _, ctas, _ = batch.info()
+    columns = sum(-(-s[0][1] // r_used) * -(-s[0][2] // 64) for s in shots)
+    assert columns >= 2 * ctas, (columns, ctas)
+    batch.apply(0, nt, dt)
+    batch.sync()
+    for run, (u_ref, rec_ref) in zip(runs, alone):
+        np.testing.assert_array_equal(run.state(nt)[0], u_ref)
+        np.testing.assert_array_equal(run.rec_trace(), rec_ref)
