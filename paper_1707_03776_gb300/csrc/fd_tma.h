@@ -13,9 +13,8 @@ namespace fdgb {
 constexpr int kTileW = 64;       // tile width along the contiguous axis d2
 constexpr int kSideHalo = 8;     // columns loaded on each side of a tile (>= M, keeps x 16-byte aligned)
 constexpr int kBoxW = kTileW + 2 * kSideHalo;
-constexpr int kMaxRows = 32;     // rows (d1) per tile at most
-// rows per tile of the single-grid kernel: its compute warps plus the
-// producer warp stay within 16 warps, so each thread can hold 128 registers
+// rows (d1) per tile at most: the compute warps plus the producer warp stay
+// within 16 warps, so each thread can hold 128 registers
 constexpr int kMaxRowsTiled = 30;
 
 // Threads of a single-grid tiled CTA: 16 per tile row (4 points each),

@@ -2,14 +2,15 @@
 //
 // A batch is a set of 3D acoustic operators -- one per shot, each on its own
 // grid (e.g. a subgrid window of a large model) -- that advance together.
-// Every time step is one launch of a persistent kernel: each CTA walks a list
-// of work items, sweeping tile columns of any shot with the same column sweep
-// as the single-grid kernel (k_sweep.cuh: ring slots and mbarrier phases run
-// on across columns), and gathering receivers of any shot from u^n in global
-// memory (no CTA writes u^n during a step).  Items are spread over the CTAs
-// by longest-processing-time-first on their cost in plane-rows, so shots of
-// uneven sizes fill the GPU together.  The whole time loop can be captured
-// once as a CUDA graph and replayed.
+// Every time step is one launch of a persistent kernel: each CTA's producer
+// warp takes work items from one list as the CTA's ring has room, and the CTA
+// sweeps tile columns of any shot with the single-grid kernel's producer and
+// consumer code (k_sweep.cuh: ring positions run on across columns, so the
+// pipeline does not drain between them), or gathers receivers of any shot
+// from u^n in global memory (no CTA writes u^n during a step).  The list is
+// in decreasing cost (plane-rows), taken longest-processing-time-first at
+// run time, so shots of uneven sizes fill the GPU together.  The whole time
+// loop can be captured once as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
