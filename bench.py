@@ -425,6 +425,7 @@ def bench_gradient(n=256, nt=1500, k=50, shots=8):
 
     # headline: all shots, checkpoints every k steps
     props = [propagator(shot, k) for shot in cfg["shots"]]
+    fused = all(fd.fd_operator_sources_fused(p.adj.handle) for p, _ in props)
     launches0 = sum(p.adj.launches + p.re.launches + p.fwd.launches for p, _ in props)
     s_all, g_all, loss_all = gradient(props, reps=2)
     launches = (sum(p.adj.launches + p.re.launches + p.fwd.launches for p, _ in props) - launches0) // 2
@@ -458,7 +459,9 @@ def bench_gradient(n=256, nt=1500, k=50, shots=8):
             "unit": "GPts/s (grid points x steps of the modelled shots per second of forward+adjoint+imaging)",
             "s_gradient_all_shots": s_all, "s_per_shot": s_all / shots, "loss": loss_all,
             "launches_per_gradient": launches,
-            "imaging": "fused into the adjoint sweep (fd_operator_apply_imaging)",
+            "imaging": ("fused into the adjoint sweep with the residual injection (fd_operator_apply_imaging)"
+                        if fused else "separate kernels after the adjoint sweep (its sources are not staged)"),
+            "adjoint_sources_fused": fused,
             "recomputed_steps_per_shot": nt,
             "per_shot": {"checkpointed_s": side["checkpointed"],
                          "whole_history_s": side["whole_history"],

@@ -367,6 +367,12 @@ fd_status fd_operator_set_tiling(fd_operator *op, int rows, int stages);
 /* The tiling in use: rows per tile, prefetch depth, CTAs per launch (tile
  * columns x d0 chunks; all 0 when the operator runs the plain kernels). */
 fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, int *stages, int *ctas);
+/* *fused = 1 when the tiled sweep injects the operator's sources itself (each
+ * CTA stages its corners in shared memory), so that fd_operator_apply_imaging
+ * also fuses the imaging condition into the sweep; 0 when injection runs as
+ * its own kernel (no sources, plain kernels, or corners that would cost the
+ * tiling its CTAs per SM).  Errors: FD_ERR_INVALID_ARG (null pointer). */
+fd_status fd_operator_sources_fused(const fd_operator *op, int *fused);
 
 /* Autotuner: time candidate tilings (tile heights 8..30 rows by prefetch
  * depths 2..4) over `nsteps` steps n = t0..t0+nsteps-1 with CUDA events on the

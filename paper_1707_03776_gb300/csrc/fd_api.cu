@@ -1089,6 +1089,14 @@ extern "C" fd_status fd_operator_get_tiling(const fd_operator *op, int *rows, in
     return FD_OK;
 }
 
+extern "C" fd_status fd_operator_sources_fused(const fd_operator *op, int *fused)
+{
+    if (!op || !fused) return set_error(FD_ERR_INVALID_ARG, "fd_operator_sources_fused: null pointer");
+    const bool plain = (op->flags & FD_FLAG_PLAIN_KERNELS) != 0 || !op->tma.ready;
+    *fused = (!plain && op->tma.has_src && op->src && op->src->npoint > 0) ? 1 : 0;
+    return FD_OK;
+}
+
 extern "C" fd_status fd_operator_autotune(fd_operator *op, int64_t t0, int64_t nsteps, double dt, int *best_rows,
                                           int *best_stages, double *best_ms_per_step)
 {

@@ -92,7 +92,8 @@ struct TmaPlan {
     SparseFused fused;
     void *fused_mem = nullptr;
     bool has_src = false;
-    int src_cap = 0;  // injected corners per tile staged in shared memory
+    int src_cap = 0;      // injected corners a CTA (tile column, d0 chunk) stages in shared memory
+    int src_cap_col = 0;  // the same for a whole tile column (the batched kernel's items)
     // tensor maps of buffers other than the two slots (out-of-place steps)
     struct CachedMap {
         const void *ptr;
@@ -141,10 +142,13 @@ int tma_occupancy(int M, int P, int threads, size_t smem);
 // Tensor map of a 3D field of the tiling `a` with a box of box_w x box_h x 1.
 fd_status tma_encode_3d(CUtensorMap *map, float *base, const TileArgs &a, int box_w, int box_h);
 
-// Injected corners of the point set `src` per tile of the tiling `a`, each
-// tile's list sorted by plane: all[off[t] .. off[t+1]) belong to tile t.
-void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vector<SrcEntry> &all,
-                        std::vector<int> &off, int &max_per_tile);
+// Injected corners of the point set `src` per (tile t, d0 chunk c) of the
+// tiling `a` cut into kz chunks, each list sorted by plane (then by owning
+// thread): all[off[t kz + c] .. off[t kz + c + 1]) belong to that CTA, and
+// all[off[t kz] .. off[(t + 1) kz]) to the whole tile column.  max_per_item
+// and max_per_column: the longest of each.
+void fused_corner_lists(const TileArgs &a, int kz, const SparseHostView *src, std::vector<SrcEntry> &all,
+                        std::vector<int> &off, int &max_per_item, int &max_per_column);
 // Copy the lists to one device allocation (mem_out, freed by the caller).
 fd_status fused_upload(const std::vector<SrcEntry> &all, const std::vector<int> &off, cudaStream_t st,
                        SparseFused &fused, void *&mem_out);

@@ -90,11 +90,12 @@ __global__ void __launch_bounds__(16 * kMaxRowsTiled + 32, 1)
     constexpr int kItem = ws_item_bar<M, P>();
     auto ITEM_FULL = [&](int s) { return smem_addr(&sm.bars[kItem + s]); };
     auto ITEM_EMPTY = [&](int s) { return smem_addr(&sm.bars[kItem + 2 + s]); };
+    // a whole column's corners: the runs of all its d0 chunks, one after another
     auto corners = [&](const ShotDesc *sd, int tile, int &s0) {
         s0 = 0;
         if (!sd->src) return 0;
-        s0 = sd->src_off[tile];
-        return sd->src_off[tile + 1] - s0;
+        s0 = sd->src_off[tile * sd->a.kz];
+        return sd->src_off[(tile + 1) * sd->a.kz] - s0;
     };
 
     if (warp == compute_warps) {
@@ -208,7 +209,7 @@ fd_status batch_plan_build(BatchPlan &bp, const std::vector<const TmaPlan *> &pl
     for (const TmaPlan *p : plans) {
         rows_max = std::max(rows_max, p->args.rows_max);
         n0_max = std::max(n0_max, p->args.n0);
-        if (p->has_src) src_cap = std::max(src_cap, p->src_cap);
+        if (p->has_src) src_cap = std::max(src_cap, p->src_cap_col);
     }
     int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);

@@ -608,8 +608,8 @@ fd_status pair_sparse_build(PairPlan &plan, const SparseHostView *src, cudaStrea
     if (!src || src->npoint <= 0) return FD_OK;
     std::vector<SrcEntry> all;
     std::vector<int> off;
-    int max_s = 0;
-    fused_corner_lists(a, src, all, off, max_s);
+    int max_s = 0, max_col = 0;
+    fused_corner_lists(a, 1, src, all, off, max_s, max_col);  // one CTA per whole column
     const size_t smem = pair_smem_layout(plan.M, plan.stages, a.rows_max, max_s, a.n0).end;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(16 * kMaxRowsTiled + 32, 1)
     const int chunk = (int)(blockIdx.x / (unsigned)ncol);
     const int z_lo = (int)((long long)chunk * a.n0 / a.kz);
     const int z_hi = (int)((long long)(chunk + 1) * a.n0 / a.kz);
-    const int s0 = src_row ? src_off[tile] : 0;
-    const int nsrc = src_row ? src_off[tile + 1] - s0 : 0;
+    const int item = tile * a.kz + chunk;  // the CTA's own corner list
+    const int s0 = src_row ? src_off[item] : 0;
+    const int nsrc = src_row ? src_off[item + 1] - s0 : 0;
     if (nsrc > src_cap) {
         // more corners than the launch staged room for
         if (threadIdx.x == 0) atomicExch(status, (int)FD_ERR_LAYOUT);
@@ -304,14 +305,23 @@ void tma_plan_release(TmaPlan &plan, cudaStream_t st)
     plan.has_src = false;
 }
 
-void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vector<SrcEntry> &all,
-                        std::vector<int> &off, int &max_per_tile)
+void fused_corner_lists(const TileArgs &a, int kz, const SparseHostView *src, std::vector<SrcEntry> &all,
+                        std::vector<int> &off, int &max_per_item, int &max_per_column)
 {
     const int tiles = a.k1 * a.k2;
+    const int items = tiles * kz;
     all.clear();
-    off.assign(tiles + 1, 0);
-    max_per_tile = 0;
+    off.assign(items + 1, 0);
+    max_per_item = 0;
+    max_per_column = 0;
     if (!src || src->npoint <= 0) return;
+    // the d0 chunk holding plane z: chunk c covers [c n0 / kz, (c + 1) n0 / kz)
+    auto chunk_of = [&](int64_t z) {
+        int c = (int)(z * kz / a.n0);
+        while (c > 0 && (int64_t)c * a.n0 / kz > z) c--;
+        while (c + 1 < kz && (int64_t)(c + 1) * a.n0 / kz <= z) c++;
+        return c;
+    };
     // tile owning grid row i1 and column i2, and that tile's first row/column
     auto owner = [&](int64_t i1, int64_t i2, int &tile, int &row0, int &col0) {
         int strip = (int)(i1 * a.k1 / a.n1);
@@ -322,7 +332,7 @@ void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vecto
         col0 = t2 * kTileW;
         tile = strip * a.k2 + t2;
     };
-    std::vector<std::vector<SrcEntry>> per(tiles);
+    std::vector<std::vector<SrcEntry>> per(items);
     for (int p = 0; p < src->npoint; p++) {
         const int64_t lin = src->base[p];
         const int64_t i0 = lin / a.s0;
@@ -341,21 +351,25 @@ void fused_corner_lists(const TileArgs &a, const SparseHostView *src, std::vecto
             e.x = (int)(x - col0);
             e.p = p;
             e.w = w;
-            per[tile].push_back(e);
+            per[(size_t)tile * kz + chunk_of(z)].push_back(e);
         }
     }
-    for (int t = 0; t < tiles; t++) {
+    // item (tile t, chunk c) = t kz + c: a tile's chunks are consecutive, so a
+    // whole column's corners are one run as well (the batched kernel sweeps
+    // whole columns)
+    for (int it = 0; it < items; it++) {
         // by plane, then by the thread owning the corner (row, 4-column
         // group): a thread finds its entries by binary search; stable, so the
         // entries of one point stay in (point, corner) order
-        std::stable_sort(per[t].begin(), per[t].end(), [](const SrcEntry &x, const SrcEntry &y) {
+        std::stable_sort(per[it].begin(), per[it].end(), [](const SrcEntry &x, const SrcEntry &y) {
             return x.z != y.z ? x.z < y.z : src_owner_key(x) < src_owner_key(y);
         });
-        off[t] = (int)all.size();
-        all.insert(all.end(), per[t].begin(), per[t].end());
-        max_per_tile = std::max(max_per_tile, (int)per[t].size());
+        off[it] = (int)all.size();
+        all.insert(all.end(), per[it].begin(), per[it].end());
+        max_per_item = std::max(max_per_item, (int)per[it].size());
+        if (it % kz == kz - 1) max_per_column = std::max(max_per_column, (int)all.size() - off[it - (kz - 1)]);
     }
-    off[tiles] = (int)all.size();
+    off[items] = (int)all.size();
 }
 
 fd_status fused_upload(const std::vector<SrcEntry> &all, const std::vector<int> &off, cudaStream_t st,
@@ -385,6 +399,7 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
     plan.has_src = false;
     plan.fused = SparseFused();
     plan.src_cap = 0;
+    plan.src_cap_col = 0;
     if (!plan.ready) return FD_OK;
     const TileArgs &a = plan.args;
     const int M = plan.M;
@@ -392,9 +407,11 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
     if (!src || src->npoint <= 0) return FD_OK;
     std::vector<SrcEntry> all;
     std::vector<int> off;
-    int max_s = 0;
-    fused_corner_lists(a, src, all, off, max_s);
-    // The tile's corners are staged in shared memory.  Staging them must
+    int max_s = 0, max_col = 0;
+    // one list per CTA (tile column and d0 chunk): a chunk stages only the
+    // corners of its own planes
+    fused_corner_lists(a, a.kz, src, all, off, max_s, max_col);
+    // The CTA's corners are staged in shared memory.  Staging them must
     // keep the CTAs per SM the tiling places (a second wave costs far more
     // than the atomic injection kernel: a receiver lattice injected by the
     // adjoint puts thousands of corners in one tile column), lowering the
@@ -417,6 +434,7 @@ fd_status tma_sparse_build(TmaPlan &plan, const SparseHostView *src, cudaStream_
     if (s != FD_OK) return s;
     plan.has_src = true;
     plan.src_cap = max_s;
+    plan.src_cap_col = max_col;
     plan.smem = tma_smem_bytes(M, plan.stages, a.rows_max, a.n0, plan.src_cap);
     return FD_OK;
 }

@@ -116,6 +116,7 @@ _SIGNATURES = [
     ("fd_operator_set_time_block", ctypes.c_int, [_vp, ctypes.c_int]),
     ("fd_operator_get_time_block", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("fd_operator_debug_stall", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("fd_operator_sources_fused", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     ("fd_operator_get_tiling", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -315,6 +316,13 @@ def fd_operator_autotune(op, t0, nsteps, dt):
     _check(lib().fd_operator_autotune(op, int(t0), int(nsteps), float(dt), ctypes.byref(r), ctypes.byref(st),
                                       ctypes.byref(ms)))
     return r.value, st.value, ms.value
+
+
+def fd_operator_sources_fused(op):
+    """True when the tiled sweep injects the operator's sources itself."""
+    f = ctypes.c_int(0)
+    _check(lib().fd_operator_sources_fused(op, ctypes.byref(f)))
+    return bool(f.value)
 
 
 def fd_operator_get_tiling(op):

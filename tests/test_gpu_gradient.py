@@ -153,3 +153,55 @@ def test_fused_imaging_equals_step_then_imaging(flags):
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
     assert np.abs(out[0][1] - grad0[..., :shape[2]].cpu().numpy()).max() > 0
+
+
+def test_receiver_lattice_is_injected_inside_the_chunked_sweep():
+    """The adjoint's sources are a receiver lattice: thousands of corners in
+    the tile columns at the receivers' depth.  On a grid small enough that the
+    planner splits d0 into chunks, each chunk's CTA stages only its own planes'
+    corners, so the sweep injects them itself (fd_operator_sources_fused) and
+    apply_imaging fuses the imaging condition.  Eight adjoint steps with imaging
+    then agree with the plain kernels (atomic injection, separate imaging) to
+    FP32 rounding (the injection sums round in another order)."""
+    import torch
+    shape = (96, 96, 96)
+    h = (10.0,) * 3
+    origin = (0.0,) * 3
+    nt, dt = 8, 1e-3
+    g = np.random.default_rng(77)
+    side = np.linspace(50.0, 900.0, 33)
+    X, Y = np.meshgrid(side, side, indexing="ij")
+    rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 105.0)], axis=1)
+    trace = g.standard_normal((nt, rec.shape[0])).astype(np.float32)
+    m = (1.0 / wl.random_smooth_velocity(shape, 5, sigma_cells=6.0, vmin=1800.0, vmax=2600.0) ** 2).astype(np.float32)
+    grid = fd.Grid(shape, h, origin)
+    hist = [torch.zeros(grid.padded_shape, dtype=torch.float32, device="cuda") for _ in range(nt + 2)]
+    for i, f in enumerate(hist):
+        f[..., :shape[2]].copy_(torch.from_numpy(wl.random_field(shape, 40 + i, smooth=1)))
+    results = []
+    for flags in (fd.FD_FLAG_REVERSE, fd.FD_FLAG_REVERSE | fd.FD_FLAG_PLAIN_KERNELS):
+        mu = fd.TimeData("mu", grid)
+        md = fd.DenseData("m", grid)
+        md.data.copy_(torch.from_numpy(m))
+        src = fd.PointData("res", grid, rec, nt)
+        src.data[:, : rec.shape[0]].copy_(torch.from_numpy(trace))
+        op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, 8, mu, md, src=src, flags=flags)
+        if not flags & fd.FD_FLAG_PLAIN_KERNELS:
+            rows, stages, ctas = fd.fd_operator_get_tiling(op.handle)
+            columns = -(-shape[1] // rows) * -(-shape[2] // 64)
+            assert ctas > columns, (rows, ctas, columns)  # d0 chunks
+            assert fd.fd_operator_sources_fused(op.handle)
+        else:
+            assert not fd.fd_operator_sources_fused(op.handle)
+        grad = torch.zeros_like(hist[0])
+        for n in range(nt - 1, -1, -1):
+            fd.fd_operator_apply_imaging(op.handle, n, dt, -1.0 / dt ** 2, hist[n].data_ptr(), hist[n + 1].data_ptr(),
+                                         hist[n + 2].data_ptr(), grad.data_ptr())
+        op.sync()
+        torch.cuda.synchronize()
+        results.append((mu.slots[0][..., :shape[2]].cpu().numpy().astype(np.float64),
+                        grad[..., :shape[2]].cpu().numpy().astype(np.float64)))
+    (ua, ga), (ub, gb) = results
+    assert np.abs(ga).max() > 0
+    assert np.linalg.norm(ua - ub) <= 1e-6 * np.linalg.norm(ub)
+    assert np.linalg.norm(ga - gb) <= 1e-6 * np.linalg.norm(gb)
