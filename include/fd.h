@@ -470,9 +470,9 @@ fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const void *frag, c
  * bytes ([tap][2 halves][16 out][8 in] BF16).  x, y and mask must be 16-byte
  * aligned (FD_ERR_LAYOUT).  status: a device int the kernel sets to
  * FD_ERR_TIMEOUT if one of its bounded waits gave up (caller clears it).
- * With 16 output channels the tensor core is bound by its shared-memory reads
- * of the activation tile and is not faster than fd_cnn_conv3d, which the
- * closure uses; this path is kept for comparison. */
+ * Each MMA takes the three d1 taps of one (d0, d2) tap side by side in N
+ * (N = 48), so a 16 -> 16 layer runs about twice as fast as fd_cnn_conv3d;
+ * the closure network uses this path by default. */
 fd_status fd_cnn_pack_weights_tc(const float *w, int cin, int cout, int flip, void *frag, void *cuda_stream);
 fd_status fd_cnn_conv3d_tc(const int64_t *shape, const void *x, const void *frag, const float *bias, int cout,
                            int relu, const void *mask, void *y, int y_fp32, int *status, void *cuda_stream);
