@@ -466,8 +466,9 @@ fd_status fd_cnn_conv3d(const int64_t *shape, const void *x, const void *frag, c
                         int relu, const void *mask, void *y, int y_fp32, void *cuda_stream);
 /* The same convolution on the 5th-generation tensor cores (tcgen05.mma with
  * tensor-memory accumulators, TMA-loaded planes): results equal
- * fd_cnn_conv3d's; weights packed by fd_cnn_pack_weights_tc into 27 * 512
- * bytes ([tap][2 halves][16 out][8 in] BF16).  x, y and mask must be 16-byte
+ * fd_cnn_conv3d's to FP32 rounding (the taps are summed in another order);
+ * weights packed by fd_cnn_pack_weights_tc into 27 * 512 bytes (per (d0 tap,
+ * d2 tap): [2 channel halves][48 = 3 d1 taps x 16 out][8 in] BF16).  x, y and mask must be 16-byte
  * aligned (FD_ERR_LAYOUT).  status: a device int the kernel sets to
  * FD_ERR_TIMEOUT if one of its bounded waits gave up (caller clears it).
  * Each MMA takes the three d1 taps of one (d0, d2) tap side by side in N
