@@ -738,7 +738,7 @@ def bench_learned(n=128, nt=2000):
     torch.cuda.synchronize()
     ms_net_mma = e0.elapsed_time(e1) / reps
     pts = float(n) ** 3
-    ch = closure.CHANNELS
+    ch = net.channels
     flops = 2.0 * 27 * pts * sum(ch[i] * ch[i + 1] for i in range(len(ch) - 1))
     flops_mma = 2.0 * 27 * pts * 16 * 16 * 4  # issued: channels padded to 16 on both sides of every layer
     peak, kind = measured_peak_bf16()

@@ -33,10 +33,10 @@ NLAYER = len(CHANNELS) - 1
 MAX_SUB = 3
 
 
-def channels(nsub=0):
+def channels(nsub=0, hidden=3):
     """Channel counts of the layers: 6 wavefield features plus 2 per model
-    descriptor in, then 16, 16, 16, 1."""
-    return (6 + 2 * int(nsub),) + CHANNELS[1:]
+    descriptor in, then `hidden` layers of 16 channels, then 1."""
+    return (6 + 2 * int(nsub),) + (16,) * int(hidden) + (1,)
 # convolutions on the tcgen05 kernel (fd_cnn_conv3d_tc) unless a caller asks
 # for the mma.sync one (fd_cnn_conv3d); they agree to FP32 rounding
 TENSOR_MEMORY = True
@@ -58,22 +58,26 @@ class ClosureNet:
     nsub > 0 the first layer also reads (s_k u, s_k du) for the first nsub
     model descriptors s_k."""
 
-    def __init__(self, seed=0, rho=1.0, nsub=0):
+    def __init__(self, seed=0, rho=1.0, nsub=0, hidden=3):
         import torch
         self.torch = torch
         if not 0 <= int(nsub) <= MAX_SUB:
             raise ValueError("nsub must be in 0..%d" % MAX_SUB)
+        if int(hidden) < 1:
+            raise ValueError("hidden must be >= 1")
         self.nsub = int(nsub)
-        self.channels = channels(nsub)
+        self.channels = channels(nsub, hidden)
+        self.nlayer = len(self.channels) - 1
         CH = self.channels
-        sizes = [27 * CH[i] * CH[i + 1] for i in range(NLAYER)]
+        L = self.nlayer
+        sizes = [27 * CH[i] * CH[i + 1] for i in range(L)]
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         n = int(self.offsets[-1])
         g = np.random.default_rng(seed)
         init = []
-        for li in range(NLAYER):
+        for li in range(L):
             cin = CH[li]
-            std = math.sqrt(2.0 / (27 * cin)) * (0.1 if li == NLAYER - 1 else 1.0)
+            std = math.sqrt(2.0 / (27 * cin)) * (0.1 if li == L - 1 else 1.0)
             init.append(g.standard_normal(sizes[li]) * std)
         self.params = torch.from_numpy(np.concatenate(init).astype(np.float32)).cuda()
         self.grads = torch.zeros(n, dtype=torch.float32, device="cuda")
@@ -82,12 +86,12 @@ class ClosureNet:
         self.adam_step = 0
         self.gb_dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
         self.frag = [torch.zeros(_frag_bytes(CH[i + 1]), dtype=torch.uint8, device="cuda")
-                     for i in range(NLAYER)]
+                     for i in range(L)]
         self.frag_t = [torch.zeros(_frag_bytes(CH[i]), dtype=torch.uint8, device="cuda")
-                       for i in range(NLAYER)]
+                       for i in range(L)]
         # tcgen05 operand layout of the same weights, forward and mirrored
-        self.frag_tc = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
-        self.frag_tc_t = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(NLAYER)]
+        self.frag_tc = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(L)]
+        self.frag_tc_t = [torch.zeros(27 * 512, dtype=torch.uint8, device="cuda") for _ in range(L)]
         self.tc_status = torch.zeros(1, dtype=torch.int32, device="cuda")
         self.rho = float(rho)
         self.vref = 3500.0
@@ -103,7 +107,7 @@ class ClosureNet:
 
     def pack(self):
         st = _stream()
-        for li in range(NLAYER):
+        for li in range(self.nlayer):
             cin, cout = self.channels[li], self.channels[li + 1]
             fd.fd_cnn_pack_weights(self.weight(li), cin, cout, 0, self.frag[li], st)
             fd.fd_cnn_pack_weights_tc(self.weight(li), cin, cout, 0, self.frag_tc[li], st)
@@ -120,13 +124,13 @@ class ClosureNet:
             raise fd.FDError(code, "a tcgen05 convolution gave up on a bounded wait")
 
     def set_weights(self, ws):
-        """Load FP32 weights [(27, cin, cout)] * NLAYER (numpy) and repack."""
+        """Load FP32 weights [(27, cin, cout)] per layer (numpy) and repack."""
         for li, w in enumerate(ws):
             self.weight(li).copy_(self.torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)))
         self.pack()
 
     def weights(self):
-        return [self.weight(li).cpu().numpy().copy() for li in range(NLAYER)]
+        return [self.weight(li).cpu().numpy().copy() for li in range(self.nlayer)]
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self.adam_step += 1
@@ -136,15 +140,15 @@ class ClosureNet:
 
 
 class Workspace:
-    """Activation and gradient buffers of the network for one grid shape:
-    h[0..3] BF16 16-channel activations, out FP32, two BF16 gradient
-    buffers."""
+    """Activation and gradient buffers of a network of `nlayer` layers for one
+    grid shape: h[0 .. nlayer-1] BF16 16-channel activations (the inputs of
+    the layers), out FP32, two BF16 gradient buffers."""
 
-    def __init__(self, shape):
+    def __init__(self, shape, nlayer=NLAYER):
         import torch
         self.shape = tuple(int(s) for s in shape)
         npts = int(np.prod(self.shape))
-        self.h = [torch.zeros((npts, 16), dtype=torch.bfloat16, device="cuda") for _ in range(NLAYER)]
+        self.h = [torch.zeros((npts, 16), dtype=torch.bfloat16, device="cuda") for _ in range(nlayer)]
         self.out = torch.zeros(npts, dtype=torch.float32, device="cuda")
         self.g = [torch.zeros((npts, 16), dtype=torch.bfloat16, device="cuda") for _ in range(2)]
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -176,8 +180,8 @@ def network_forward(net, ws, stream=None, tensor_memory=None):
     one (False); the two agree to FP32 rounding."""
     st = stream or _stream()
     tensor_memory = TENSOR_MEMORY if tensor_memory is None else tensor_memory
-    for li in range(NLAYER):
-        last = li == NLAYER - 1
+    for li in range(net.nlayer):
+        last = li == net.nlayer - 1
         y = ws.out if last else ws.h[li + 1]
         if tensor_memory:
             fd.fd_cnn_conv3d_tc(ws.shape, ws.h[li], net.frag_tc[li], None, net.channels[li + 1], 0 if last else 1, None,
@@ -193,7 +197,7 @@ def network_backward(net, ws, stream=None, tensor_memory=None):
     st = stream or _stream()
     tensor_memory = TENSOR_MEMORY if tensor_memory is None else tensor_memory
     cur = 0
-    for li in range(NLAYER - 1, -1, -1):
+    for li in range(net.nlayer - 1, -1, -1):
         cin, cout = net.channels[li], net.channels[li + 1]
         fd.fd_cnn_conv3d_wgrad(ws.shape, ws.h[li], ws.g[cur], cin, cout, net.grad(li), net.gb_dummy, st)
         if li > 0:
@@ -230,7 +234,7 @@ class ClosureOperator:
         self.op = fd.Operator(fd.FD_ACOUSTIC_LEAPFROG, c["space_order"], self.u, self.m, self.eta, src=self.src,
                               rec=self.rec, flags=flags)
         self.sub = descriptor_slots(self.grid, c["sub"][: net.nsub]) if net.nsub else None
-        self.ws = Workspace(self.shape)
+        self.ws = Workspace(self.shape, net.nlayer)
 
     def run(self, nt=None, learned=True):
         """From rest: nt steps (default: the config's), each the coarse update
@@ -362,7 +366,7 @@ def train(net, data, iters, batch=4, lr=2e-3, seed=0, log_every=0, lr_final=None
     so that the correction does not react to grid-scale content the clean
     samples never show (which a rollout otherwise amplifies)."""
     torch = net.torch
-    ws = Workspace(data.shape)
+    ws = Workspace(data.shape, net.nlayer)
     g = np.random.default_rng(seed)
     st = _stream()
     hist = []
