@@ -845,9 +845,11 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         # each step (one forward call: host model in, traces out) timed on its
-        # own; the median of three, because the host-side part of a call (the
-        # copies and the launches) varies from call to call
-        e_steps = 3
+        # own; the median of five, because the host-side part of a call (the
+        # copies and the launches) varies from call to call: on some hosts a
+        # 1 GB copy from pinned memory takes 6 ms in one call and 45 ms in
+        # the next
+        e_steps = 5
         model.forward(m_h, eta_h, src_h, cfg["dt"])  # warm
         barrier()
         els, phases = [], []
