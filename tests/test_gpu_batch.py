@@ -157,3 +157,50 @@ def test_batch_sweeps_several_columns_per_cta(so, rows, stages):
     for run, (u_ref, rec_ref) in zip(runs, alone):
         np.testing.assert_array_equal(run.state(nt)[0], u_ref)
         np.testing.assert_array_equal(run.rec_trace(), rec_ref)
+
+
+def test_batch_mixed_and_degenerate_shots():
+    """Shots without sources, without receivers, and on degenerate windows
+    (a few planes, rows or columns; ragged against the 64-column tiles) in one
+    batch: every shot's field and traces equal its individual run bit for
+    bit."""
+    nt = 30
+    h = (10.0,) * 3
+    dt = 0.3 * 10.0 / 4500.0
+    specs = [((5, 6, 7), True, True), ((2, 33, 64), True, False), ((40, 52, 70), False, True),
+             ((17, 3, 130), True, True), ((9, 40, 5), False, False)]
+    shots = []
+    for i, (shape, with_src, with_rec) in enumerate(specs):
+        v = wl.random_smooth_velocity(shape, 60 + i, sigma_cells=2.0, vmin=1500.0, vmax=4500.0)
+        m = (1.0 / v ** 2).astype(np.float32)
+        eta = (m.astype(np.float64) * wl.sponge_sigma(shape, h, 1, 4500.0, ref_width=40)).astype(np.float32)
+        ext = [(n - 1) * 10.0 for n in shape]
+        src = np.array([[0.5 * ext[0], 0.5 * ext[1], 0.4 * ext[2]]]) if with_src else None
+        wav = wl.ricker(nt, dt, 25.0).astype(np.float32).reshape(nt, 1) if with_src else None
+        rec = wl.random_points(shape, h, (0.0,) * 3, 7, 80 + i) if with_rec else None
+        shots.append((shape, m, eta, src, wav, rec))
+
+    def make(sh):
+        shape, m, eta, src, wav, rec = sh
+        return AcousticRun(shape, h, None, 8, m, eta, src, wav, rec, nt)
+
+    tiled = []
+    for sh in shots:
+        r = make(sh)
+        if fd.fd_operator_get_tiling(r.op.handle)[0] > 0:
+            tiled.append(sh)
+        del r
+    assert len(tiled) >= 4, [s[0] for s in tiled]
+    alone = []
+    for sh in tiled:
+        run = make(sh)
+        run.run(0, nt, dt)
+        alone.append((run.state(nt)[0], run.rec_trace() if sh[5] is not None else None))
+    runs = [make(sh) for sh in tiled]
+    batch = fd.Batch([r.op for r in runs], rows=12, stages=3)
+    batch.apply(0, nt, dt)
+    batch.sync()
+    for run, (u_ref, rec_ref) in zip(runs, alone):
+        np.testing.assert_array_equal(run.state(nt)[0], u_ref)
+        if rec_ref is not None:
+            np.testing.assert_array_equal(run.rec_trace(), rec_ref)
