@@ -72,4 +72,6 @@ def test_network_full_size_sampled_against_oracle():
     got = np.array(got, dtype=np.float64)
     want = np.array(want)
     assert np.all(np.isfinite(got)) and np.linalg.norm(want) > 0
+    print("%d sampled outputs: relative L2 %.3e, max abs %.3e of max %.3e" % (
+        len(got), np.linalg.norm(got - want) / np.linalg.norm(want), np.abs(got - want).max(), np.abs(want).max()))
     assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want), np.linalg.norm(got - want) / np.linalg.norm(want)

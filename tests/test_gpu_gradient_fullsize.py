@@ -15,8 +15,11 @@ operators on small grids: test_gpu_gradient.py, test_oracle_gradient.py).
 * The objective J(m) = 1/2 |F(m) s - d_obs|^2, d_obs the traces of the true
   model, against its adjoint-state gradient g along dm = m_true - m0:
   - the Taylor remainder J(m0 + h dm) - J(m0) - h <g, dm> falls as h^2;
-  - central differences (J(m0 + h dm) - J(m0 - h dm)) / 2h, extrapolated in h
-    (their error is A h^2 + O(h^4)), equal <g, dm>.
+  - central differences c(h) = (J(m0 + h dm) - J(m0 - h dm)) / 2h at
+    h = 0.4, 0.2, 0.1 (error A h^2 + B h^4 + ...), Richardson-extrapolated
+    twice, equal <g, dm>.  J is far from quadratic along dm on this
+    geometry (c(h) changes sign between h = 0.1 and 0.4), so a single
+    extrapolation would leave an h^4 error of a few 1e-3.
 
 Tolerances, from the FP32 arithmetic.  Receiver traces after a full run
 carry a relative L2 error delta <= 1e-4 (the full-run gate of the 512^3
@@ -25,16 +28,20 @@ workload measured 3e-5 after 1000 steps).
     the adjoint run's delta on F^T r, amplified by
     kappa = sum |s_i (F^T r)_i| / |sum s_i (F^T r)_i|, the cancellation of
     that sum.  Bound: 2 delta (1 + kappa), with kappa measured.
-  - Objective: each J carries an absolute error <= 2 delta |d| |r| (r the
-    residual; |r| is about a fifth of |d| on this geometry).  The Taylor
-    ratios are checked only where the remainder exceeds twice that bound.
-    The bound is pessimistic: the rounding errors of the traces are not
-    aligned with the residual, so their inner product with it is far smaller.
+  - Objective: the rounding error of J is measured, not bounded: the same
+    objective through the plain kernels (another FP32 rounding of every
+    step) differs from the tiled one by about that error.  The bound
+    2 delta |d| |r| would be far too pessimistic, because the traces'
+    rounding errors are not aligned with the residual r.  The Taylor ratios
+    are checked where the remainder exceeds 20 times the measured error.
+    The doubly extrapolated difference weighs the J values by at most
+    (64/0.1 + 20/0.2 + 1/0.4) / 45 < 17 per unit of J error.  Twice the
+    measured error times that enters its tolerance.
   - Gradient: <g, dm> sums mu^n (u^n - 2u^{n-1} + u^{n-2}) over 1500 steps.
     The second time difference divides the fields' relative error by
-    (omega dt)^2, about 0.05 at the wavelet's upper frequency: 2e-3 per term,
-    averaging down over the sum.  The gradient is therefore held to 5e-3 of
-    the extrapolated differences.
+    (omega dt)^2, about 0.05 at the wavelet's upper frequency: 2e-3 per
+    term, averaging down over the sum.  The gradient is therefore held to
+    2e-3 of the extrapolated differences, plus their rounding.
 """
 import numpy as np
 import pytest
@@ -46,7 +53,7 @@ from paper_1707_03776_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 DELTA = 1e-4       # relative L2 error of receiver traces after a full run (FP32)
-GRAD_TOL = 5e-3    # <g, dm> against the extrapolated central differences
+GRAD_TOL = 2e-3    # <g, dm> against the extrapolated central differences
 
 
 @pytest.fixture(scope="module")
@@ -77,6 +84,7 @@ def test_forward_adjoint_dot_product_full_size(cfg):
     kappa = float(np.abs(terms).sum()) / abs(rhs)
     assert lhs > 0 and np.isfinite(kappa)
     tol = 2 * DELTA * (1 + kappa)
+    print("dot product: relative mismatch %.3e, kappa %.2f, tolerance %.3e" % (abs(lhs - rhs) / lhs, kappa, tol))
     assert abs(lhs - rhs) <= tol * lhs, (lhs, rhs, kappa, abs(lhs - rhs) / lhs)
 
 
@@ -104,23 +112,34 @@ def test_gradient_taylor_and_central_differences_full_size(cfg):
     dm = m_true - m0
     gdm = float((m.grad.double() * dm.double()).sum())
     J0, rn = objective(m0)
-    noise = 2 * DELTA * float(d64.norm()) * rn
     assert J0 > 0 and gdm != 0
+    # the rounding error of J: the same objective through the plain kernels
+    plain = Propagator(cfg["shape"], cfg["spacing"], cfg["origin"], 8, Shot(cfg["shots"][0], cfg["wavelet"],
+                       cfg["rec_coords"]), nt, dt, checkpoint_every=50, flags=fd.FD_FLAG_PLAIN_KERNELS)
+    plain.set_damping(cfg["eta"])
+    plain.set_model(m0)
+    res = plain.forward().double() - d64
+    noise = abs(0.5 * float((res * res).sum()) - J0)
+    del plain, res
+    torch.cuda.empty_cache()
 
     hs = (0.4, 0.2, 0.1)
     Jp = [objective(m0 + hh * dm)[0] for hh in hs]
     Jm = [objective(m0 - hh * dm)[0] for hh in hs]
     # Taylor remainder: second order in h wherever it stands above the noise
     e2 = [abs(jp - J0 - hh * gdm) for jp, hh in zip(Jp, hs)]
-    assert e2[0] > 2 * noise, (e2, noise)
     checked = 0
     for i in range(len(hs) - 1):
-        if e2[i + 1] > 2 * noise:
+        if e2[i + 1] > 20 * noise:
             assert 2.8 <= e2[i] / e2[i + 1] <= 6.0, (e2, noise)
             checked += 1
-    assert checked >= 1, (e2, noise)
-    # central differences, Richardson-extrapolated from h = 0.2 and 0.1
+    assert checked == len(hs) - 1, (e2, noise)
+    # central differences, Richardson-extrapolated twice (h = 0.4, 0.2, 0.1)
     c = [(jp - jm) / (2 * hh) for jp, jm, hh in zip(Jp, Jm, hs)]
-    c_star = (4 * c[2] - c[1]) / 3
-    tol = GRAD_TOL + noise / (hs[2] * abs(gdm))
+    r1 = [(4 * c[i + 1] - c[i]) / 3 for i in range(2)]
+    c_star = (16 * r1[1] - r1[0]) / 15
+    tol = GRAD_TOL + 2 * 17 * noise / abs(gdm)
+    print("|r|/|d| %.3f; Taylor remainders %s (J rounding %.3e); central differences %s -> %.6e vs <g, dm> %.6e: "
+          "relative %.3e, tolerance %.3e" % (rn / float(d64.norm()), ["%.4e" % e for e in e2], noise,
+                                             ["%.6e" % x for x in c], c_star, gdm, abs(c_star - gdm) / abs(gdm), tol))
     assert abs(c_star - gdm) <= tol * abs(gdm), (c, c_star, gdm, abs(c_star - gdm) / abs(gdm))
