@@ -74,7 +74,7 @@ def test_every_profile_gives_a_command_that_runs_committed_files_only():
     for f, blocks in cmds.items():
         assert blocks, "%s has no command" % f
         text = "\n".join(blocks).replace("\\\n", " ")
-        assert "_work" not in text and "gpurun" not in text, f
+        assert "_work" not in text, f
         for line in text.splitlines():
             for m in re.finditer(r"python (?:-m ([\w.]+)|([\w/]+\.py))", line):
                 if m.group(1):
