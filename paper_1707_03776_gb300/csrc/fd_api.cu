@@ -1051,6 +1051,24 @@ extern "C" fd_status fd_imaging_accumulate(const fd_grid *g, double scale, const
     return FD_OK;
 }
 
+extern "C" fd_status fd_imaging_accumulate2(const fd_grid *g, double scale, const void *mu_a, const void *mu_b,
+                                            const void *u0, const void *u1, const void *u2, const void *u3,
+                                            void *grad, void *cuda_stream)
+{
+    if (!g || !mu_a || !mu_b || !u0 || !u1 || !u2 || !u3 || !grad)
+        return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate2: null pointer");
+    for (const void *p : {mu_a, mu_b, u0, u1, u2, u3, (const void *)grad})
+        if (((uintptr_t)p) % 16 != 0) return set_error(FD_ERR_LAYOUT, "fd_imaging_accumulate2: buffer not aligned");
+    for (const void *p : {mu_a, mu_b, u0, u1, u2, u3})
+        if (p == grad) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate2: grad aliases an input");
+    if (!std::isfinite(scale)) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate2: scale not finite");
+    FD_CUDA(launch_imaging2(geom_of(*g), (float)scale, (const float *)mu_a, (const float *)mu_b, (const float *)u0,
+                            (const float *)u1, (const float *)u2, (const float *)u3, (float *)grad,
+                            (cudaStream_t)cuda_stream),
+            "fd_imaging_accumulate2");
+    return FD_OK;
+}
+
 extern "C" fd_status fd_operator_debug_stall(fd_operator *op, int plane)
 {
     if (!op || plane < -1) return set_error(FD_ERR_INVALID_ARG, "fd_operator_debug_stall: bad arguments");

@@ -79,6 +79,7 @@ _SIGNATURES = [
     ("fd_interpolate_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _c_f64p, _vp, _vp, _vp]),
     ("fd_operator_step", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp]),
     ("fd_imaging_accumulate", ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fd_imaging_accumulate2", ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("fd_operator_apply_imaging", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _vp, _vp,
                                                  _vp, _vp]),
     ("fd_operator_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -297,6 +298,13 @@ def fd_imaging_accumulate(grid, scale, mu, u0, u1, u2, grad, stream=0):
     """grad += scale * mu * (u0 - 2 u1 + u2) (device pointers)."""
     _check(lib().fd_imaging_accumulate(grid, float(scale), int(mu), int(u0), int(u1), int(u2), int(grad),
                                        int(stream) or None))
+
+
+def fd_imaging_accumulate2(grid, scale, mu_a, mu_b, u0, u1, u2, u3, grad, stream=0):
+    """grad += scale * mu_a * (u0 - 2 u1 + u2), then += scale * mu_b * (u1 - 2 u2 + u3): the
+    imaging of adjoint steps n and n-1 in one pass (device pointers)."""
+    _check(lib().fd_imaging_accumulate2(grid, float(scale), int(mu_a), int(mu_b), int(u0), int(u1), int(u2),
+                                        int(u3), int(grad), int(stream) or None))
 
 
 def fd_operator_apply_imaging(op, n, dt, scale, u0, u1, u2, grad):

@@ -11,8 +11,11 @@ segments from last to first; inside each segment the forward states are
 recomputed from its checkpoint with out-of-place steps (fd_operator_step) into
 a segment buffer, and the imaging condition
     dJ/dm += -(1/dt^2) mu^n (u^n - 2u^{n-1} + u^{n-2})
-is accumulated in the same pass as every adjoint step
-(fd_operator_apply_imaging: fused into the tiled sweep).
+is accumulated in the same pass as every adjoint step where the tiled sweep
+injects the residual itself (fd_operator_apply_imaging: fused into the
+sweep); otherwise two adjoint steps run first and one pass images both
+(fd_imaging_accumulate2), which reads each forward state and the gradient
+once for the two steps.  Either way the gradient is the same bit for bit.
 
 Every step of the path runs in libfdgb's kernels; torch provides the device
 memory (fields, checkpoints, the segment buffer) and the autograd plumbing.
@@ -79,6 +82,7 @@ class Propagator:
             # the whole history: hist[i] holds the state of time i-1 (-1 .. nt)
             self.hist = torch.zeros((self.nt + 2,) + ps, dtype=torch.float32, device="cuda")
         self.grad = fd.DenseData("grad", self.grid)
+        self.stream = torch.cuda.current_stream().cuda_stream
 
     def set_damping(self, eta):
         """Damping eta (held fixed by the gradient)."""
@@ -135,13 +139,7 @@ class Propagator:
         scale = -1.0 / (self.dt * self.dt)
         if self.k == 0:
             hist = self.hist
-            gp = self.grad.slots[0].data_ptr()
-            for n in range(self.nt - 1, -1, -1):
-                if n >= 1:
-                    fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, hist[n + 1].data_ptr(),
-                                                 hist[n].data_ptr(), hist[n - 1].data_ptr(), gp)
-                else:
-                    self.adj.apply(n, 1, self.dt)
+            self._adjoint_steps(self.nt - 1, 0, lambda t: hist[t + 1].data_ptr(), scale)
             return self.grad.data
         k = self.k
         seg = self.seg
@@ -159,15 +157,32 @@ class Propagator:
                     continue
                 fd.fd_operator_step(self.re.handle, t, self.dt, seg[i].data_ptr(), seg[i - 1].data_ptr(),
                                     seg[i + 1].data_ptr())
-            for n in range(n_hi - 1, n_lo - 1, -1):
-                if n >= 1:
-                    i = n - (n_lo - 2)
-                    fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, seg[i].data_ptr(),
-                                                 seg[i - 1].data_ptr(), seg[i - 2].data_ptr(),
-                                                 self.grad.slots[0].data_ptr())
-                else:
-                    self.adj.apply(n, 1, self.dt)
+            self._adjoint_steps(n_hi - 1, n_lo, lambda t, lo=n_lo: seg[t - (lo - 2)].data_ptr(), scale)
         return self.grad.data
+
+    def _adjoint_steps(self, n_top, n_bot, state, scale):
+        """Adjoint steps n_top .. n_bot (backward) with the imaging condition;
+        state(t) is the device pointer of the forward state of time t, for
+        t >= n_bot - 2."""
+        gp = self.grad.slots[0].data_ptr()
+        paired = not fd.fd_operator_sources_fused(self.adj.handle)
+        n = n_top
+        while n >= n_bot:
+            if paired and n - 1 >= max(n_bot, 1):
+                # steps n and n-1, then one pass images both; the adjoint
+                # state of time t is in slot t % 2
+                self.adj.apply(n - 1, 2, self.dt)
+                fd.fd_imaging_accumulate2(self.grid.handle, scale, self.mu.slots[n % 2].data_ptr(),
+                                          self.mu.slots[(n - 1) % 2].data_ptr(), state(n), state(n - 1),
+                                          state(n - 2), state(n - 3), gp, self.stream)
+                n -= 2
+            elif n >= 1:
+                fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, state(n), state(n - 1),
+                                             state(n - 2), gp)
+                n -= 1
+            else:
+                self.adj.apply(n, 1, self.dt)
+                n -= 1
 
 
 def _autograd_function():
