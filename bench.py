@@ -460,8 +460,8 @@ def bench_gradient(n=256, nt=1500, k=50, shots=8):
             "s_gradient_all_shots": s_all, "s_per_shot": s_all / shots, "loss": loss_all,
             "launches_per_gradient": launches,
             "imaging": ("fused into the adjoint sweep with the residual injection (fd_operator_apply_imaging)"
-                        if fused else "two adjoint steps, then one pass imaging both (fd_imaging_accumulate2; the sweep "
-                        "does not stage the adjoint's sources)"),
+                        if fused else "up to four adjoint steps out of place, then one pass imaging them "
+                        "(fd_imaging_accumulate_steps; the sweep does not stage the adjoint's sources)"),
             "adjoint_sources_fused": fused,
             "recomputed_steps_per_shot": nt,
             "per_shot": {"checkpointed_s": side["checkpointed"],

@@ -337,18 +337,19 @@ fd_status fd_operator_step(fd_operator *op, int64_t n, double dt, const void *u_
  * Errors: FD_ERR_INVALID_ARG, FD_ERR_LAYOUT, FD_ERR_CUDA. */
 fd_status fd_imaging_accumulate(const fd_grid *grid, double scale, const void *mu, const void *u0,
                                 const void *u1, const void *u2, void *grad, void *cuda_stream);
-/* The imaging condition above for two consecutive adjoint steps in one pass:
- * grad += scale * mu_a * (u0 - 2 u1 + u2), then
- * grad += scale * mu_b * (u1 - 2 u2 + u3), with mu_a, mu_b the adjoint states
- * of times n and n-1 and u0, u1, u2, u3 the forward states of times n .. n-3.
- * Each forward state and grad are read once for both terms: 32 bytes per node
- * instead of 2 x 24.  The result equals fd_imaging_accumulate for step n
- * followed by step n-1, bit for bit.  Same layout as fd_imaging_accumulate;
- * grad must not alias an input.  Enqueued on cuda_stream.
- * Errors: FD_ERR_INVALID_ARG, FD_ERR_LAYOUT, FD_ERR_CUDA. */
-fd_status fd_imaging_accumulate2(const fd_grid *grid, double scale, const void *mu_a, const void *mu_b,
-                                 const void *u0, const void *u1, const void *u2, const void *u3, void *grad,
-                                 void *cuda_stream);
+/* The imaging condition above for k consecutive adjoint steps (1 <= k <= 4)
+ * in one pass: for j = 0 .. k-1 in turn,
+ *   grad += scale * mu[j] * (u[j] - 2 u[j+1] + u[j+2]),
+ * with mu[j] the adjoint state of time n - j (k pointers) and u[i] the
+ * forward state of time n - i (k + 2 pointers; host arrays of device
+ * pointers).  Each forward state and grad are read once for the k steps:
+ * 4 (2k + 4) bytes per node instead of 24 k.  The result equals
+ * fd_imaging_accumulate for steps n, n-1, ..., n-k+1 in turn, bit for bit.
+ * Same layout as fd_imaging_accumulate; grad must not alias an input.
+ * Enqueued on cuda_stream.  Errors: FD_ERR_INVALID_ARG, FD_ERR_LAYOUT,
+ * FD_ERR_CUDA. */
+fd_status fd_imaging_accumulate_steps(const fd_grid *grid, double scale, int k, const void *const *mu,
+                                      const void *const *u, void *grad, void *cuda_stream);
 
 /* Step n of the operator (as fd_operator_apply(op, n, 1, dt)) with the
  * imaging condition above accumulated from the field the step writes:

@@ -1051,21 +1051,29 @@ extern "C" fd_status fd_imaging_accumulate(const fd_grid *g, double scale, const
     return FD_OK;
 }
 
-extern "C" fd_status fd_imaging_accumulate2(const fd_grid *g, double scale, const void *mu_a, const void *mu_b,
-                                            const void *u0, const void *u1, const void *u2, const void *u3,
-                                            void *grad, void *cuda_stream)
+extern "C" fd_status fd_imaging_accumulate_steps(const fd_grid *g, double scale, int k, const void *const *mu,
+                                                 const void *const *u, void *grad, void *cuda_stream)
 {
-    if (!g || !mu_a || !mu_b || !u0 || !u1 || !u2 || !u3 || !grad)
-        return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate2: null pointer");
-    for (const void *p : {mu_a, mu_b, u0, u1, u2, u3, (const void *)grad})
-        if (((uintptr_t)p) % 16 != 0) return set_error(FD_ERR_LAYOUT, "fd_imaging_accumulate2: buffer not aligned");
-    for (const void *p : {mu_a, mu_b, u0, u1, u2, u3})
-        if (p == grad) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate2: grad aliases an input");
-    if (!std::isfinite(scale)) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate2: scale not finite");
-    FD_CUDA(launch_imaging2(geom_of(*g), (float)scale, (const float *)mu_a, (const float *)mu_b, (const float *)u0,
-                            (const float *)u1, (const float *)u2, (const float *)u3, (float *)grad,
-                            (cudaStream_t)cuda_stream),
-            "fd_imaging_accumulate2");
+    if (!g || !mu || !u || !grad) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate_steps: null pointer");
+    if (k < 1 || k > 4) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate_steps: k = %d (1..4)", k);
+    const float *pm[4] = {};
+    const float *pu[6] = {};
+    for (int i = 0; i < k + 2; i++) {
+        const void *q[2] = {i < k ? mu[i] : nullptr, u[i]};
+        for (int s = 0; s < 2; s++) {
+            if (s == 0 && i >= k) continue;
+            if (!q[s]) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate_steps: null buffer");
+            if (((uintptr_t)q[s]) % 16 != 0)
+                return set_error(FD_ERR_LAYOUT, "fd_imaging_accumulate_steps: buffer not aligned");
+            if (q[s] == grad) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate_steps: grad aliases an input");
+        }
+        if (i < k) pm[i] = (const float *)mu[i];
+        pu[i] = (const float *)u[i];
+    }
+    if (((uintptr_t)grad) % 16 != 0) return set_error(FD_ERR_LAYOUT, "fd_imaging_accumulate_steps: grad not aligned");
+    if (!std::isfinite(scale)) return set_error(FD_ERR_INVALID_ARG, "fd_imaging_accumulate_steps: scale not finite");
+    FD_CUDA(launch_imaging_steps(geom_of(*g), (float)scale, k, pm, pu, (float *)grad, (cudaStream_t)cuda_stream),
+            "fd_imaging_accumulate_steps");
     return FD_OK;
 }
 

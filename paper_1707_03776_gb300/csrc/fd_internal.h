@@ -56,8 +56,8 @@ cudaError_t launch_acoustic_plain(int half_width, const Geom &g, const Coef &cf,
 // grad += scale * mu * (u0 - 2 u1 + u2)
 cudaError_t launch_imaging(const Geom &g, float scale, const float *mu, const float *u0,
                            const float *u1, const float *u2, float *grad, cudaStream_t st);
-cudaError_t launch_imaging2(const Geom &g, float scale, const float *mu_a, const float *mu_b, const float *u0,
-                            const float *u1, const float *u2, const float *u3, float *grad, cudaStream_t st);
+cudaError_t launch_imaging_steps(const Geom &g, float scale, int k, const float *const *mu, const float *const *u,
+                                 float *grad, cudaStream_t st);
 cudaError_t launch_diffusion_plain(int half_width, const Geom &g, const Coef &cf, float adt,
                                    const float *u, float *u_out, cudaStream_t st);
 

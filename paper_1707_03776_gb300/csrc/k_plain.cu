@@ -129,17 +129,20 @@ __global__ void acoustic_plain_kernel(Geom g, Coef cf, const float *__restrict__
     }
 }
 
-// The imaging condition of two consecutive adjoint steps in one pass:
-// grad += scale * mu_a * (u0 - 2 u1 + u2), then grad += scale * mu_b * (u1 -
-// 2 u2 + u3), with mu_a, mu_b the adjoint states of times n and n - 1 and
-// u0..u3 the forward states of times n..n-3.  Each forward state and grad are
-// read once for both steps (32 bytes per point instead of 2 x 24); the two
-// FMA chains are imaging_kernel's, in its order, so the result equals two
-// imaging_kernel launches bit for bit.
-__global__ void imaging2_kernel(Geom g, float scale, const float *__restrict__ mu_a,
-                                const float *__restrict__ mu_b, const float *__restrict__ u0,
-                                const float *__restrict__ u1, const float *__restrict__ u2,
-                                const float *__restrict__ u3, float *__restrict__ grad)
+// The imaging condition of K consecutive adjoint steps in one pass: for
+// j = 0 .. K-1 in turn, grad += scale * mu[j] * (u[j] - 2 u[j+1] + u[j+2]),
+// with mu[j] the adjoint state of time n - j and u[i] the forward state of
+// time n - i.  Each forward state and grad are read once for the K steps
+// (4 (2K + 4) bytes per point instead of 24 K); every step's FMA chain is
+// imaging_kernel's, in its order, so the result equals K imaging_kernel
+// launches (steps n, n-1, ...) bit for bit.
+struct ImagingSteps {
+    const float *mu[4];
+    const float *u[6];
+};
+
+template <int K>
+__global__ void imaging_steps_kernel(Geom g, float scale, ImagingSteps p, float *__restrict__ grad)
 {
     const int64_t rows = g.n[0] * g.n[1];
     const int64_t groups = (g.n[2] + 3) / 4;  // float4 groups per row
@@ -151,27 +154,28 @@ __global__ void imaging2_kernel(Geom g, float scale, const float *__restrict__ m
         const int64_t i1 = row - i0 * g.n[1];
         const int64_t at = i0 * g.s0 + i1 * g.s1 + c0;
         if (c0 + 4 <= g.n[2]) {
-            const float4 ma = *reinterpret_cast<const float4 *>(mu_a + at);
-            const float4 mb = *reinterpret_cast<const float4 *>(mu_b + at);
-            const float4 a = *reinterpret_cast<const float4 *>(u0 + at);
-            const float4 b = *reinterpret_cast<const float4 *>(u1 + at);
-            const float4 e = *reinterpret_cast<const float4 *>(u2 + at);
-            const float4 f = *reinterpret_cast<const float4 *>(u3 + at);
+            float4 u[K + 2];
+#pragma unroll
+            for (int i = 0; i < K + 2; i++) u[i] = *reinterpret_cast<const float4 *>(p.u[i] + at);
             float4 gr = *reinterpret_cast<const float4 *>(grad + at);
-            gr.x = fmaf(scale * ma.x, fmaf(-2.0f, b.x, a.x) + e.x, gr.x);
-            gr.y = fmaf(scale * ma.y, fmaf(-2.0f, b.y, a.y) + e.y, gr.y);
-            gr.z = fmaf(scale * ma.z, fmaf(-2.0f, b.z, a.z) + e.z, gr.z);
-            gr.w = fmaf(scale * ma.w, fmaf(-2.0f, b.w, a.w) + e.w, gr.w);
-            gr.x = fmaf(scale * mb.x, fmaf(-2.0f, e.x, b.x) + f.x, gr.x);
-            gr.y = fmaf(scale * mb.y, fmaf(-2.0f, e.y, b.y) + f.y, gr.y);
-            gr.z = fmaf(scale * mb.z, fmaf(-2.0f, e.z, b.z) + f.z, gr.z);
-            gr.w = fmaf(scale * mb.w, fmaf(-2.0f, e.w, b.w) + f.w, gr.w);
+#pragma unroll
+            for (int j = 0; j < K; j++) {
+                const float4 m4 = *reinterpret_cast<const float4 *>(p.mu[j] + at);
+                const float4 a = u[j], b = u[j + 1], e = u[j + 2];
+                gr.x = fmaf(scale * m4.x, fmaf(-2.0f, b.x, a.x) + e.x, gr.x);
+                gr.y = fmaf(scale * m4.y, fmaf(-2.0f, b.y, a.y) + e.y, gr.y);
+                gr.z = fmaf(scale * m4.z, fmaf(-2.0f, b.z, a.z) + e.z, gr.z);
+                gr.w = fmaf(scale * m4.w, fmaf(-2.0f, b.w, a.w) + e.w, gr.w);
+            }
             *reinterpret_cast<float4 *>(grad + at) = gr;
         } else {
             for (int64_t k = 0; c0 + k < g.n[2]; k++) {
                 const int64_t i = at + k;
-                const float t = fmaf(scale * mu_a[i], fmaf(-2.0f, u1[i], u0[i]) + u2[i], grad[i]);
-                grad[i] = fmaf(scale * mu_b[i], fmaf(-2.0f, u2[i], u1[i]) + u3[i], t);
+                float t = grad[i];
+#pragma unroll
+                for (int j = 0; j < K; j++)
+                    t = fmaf(scale * p.mu[j][i], fmaf(-2.0f, p.u[j + 1][i], p.u[j][i]) + p.u[j + 2][i], t);
+                grad[i] = t;
             }
         }
     }
@@ -350,11 +354,21 @@ cudaError_t launch_imaging(const Geom &g, float scale, const float *mu, const fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_imaging2(const Geom &g, float scale, const float *mu_a, const float *mu_b, const float *u0,
-                            const float *u1, const float *u2, const float *u3, float *grad, cudaStream_t st)
+cudaError_t launch_imaging_steps(const Geom &g, float scale, int k, const float *const *mu, const float *const *u,
+                                 float *grad, cudaStream_t st)
 {
-    int64_t total = g.n[0] * g.n[1] * ((g.n[2] + 3) / 4);
-    imaging2_kernel<<<grid_stride_blocks(total), kThreads, 0, st>>>(g, scale, mu_a, mu_b, u0, u1, u2, u3, grad);
+    if (k < 1 || k > 4) return cudaErrorInvalidValue;
+    ImagingSteps p{};
+    for (int j = 0; j < k; j++) p.mu[j] = mu[j];
+    for (int i = 0; i < k + 2; i++) p.u[i] = u[i];
+    const int64_t total = g.n[0] * g.n[1] * ((g.n[2] + 3) / 4);
+    const int blocks = grid_stride_blocks(total);
+    switch (k) {
+    case 1: imaging_steps_kernel<1><<<blocks, kThreads, 0, st>>>(g, scale, p, grad); break;
+    case 2: imaging_steps_kernel<2><<<blocks, kThreads, 0, st>>>(g, scale, p, grad); break;
+    case 3: imaging_steps_kernel<3><<<blocks, kThreads, 0, st>>>(g, scale, p, grad); break;
+    default: imaging_steps_kernel<4><<<blocks, kThreads, 0, st>>>(g, scale, p, grad); break;
+    }
     return cudaGetLastError();
 }
 

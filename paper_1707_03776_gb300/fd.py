@@ -79,7 +79,7 @@ _SIGNATURES = [
     ("fd_interpolate_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _c_f64p, _vp, _vp, _vp]),
     ("fd_operator_step", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp]),
     ("fd_imaging_accumulate", ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
-    ("fd_imaging_accumulate2", ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fd_imaging_accumulate_steps", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _vp]),
     ("fd_operator_apply_imaging", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _vp, _vp,
                                                  _vp, _vp]),
     ("fd_operator_set_tiling", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -300,11 +300,16 @@ def fd_imaging_accumulate(grid, scale, mu, u0, u1, u2, grad, stream=0):
                                        int(stream) or None))
 
 
-def fd_imaging_accumulate2(grid, scale, mu_a, mu_b, u0, u1, u2, u3, grad, stream=0):
-    """grad += scale * mu_a * (u0 - 2 u1 + u2), then += scale * mu_b * (u1 - 2 u2 + u3): the
-    imaging of adjoint steps n and n-1 in one pass (device pointers)."""
-    _check(lib().fd_imaging_accumulate2(grid, float(scale), int(mu_a), int(mu_b), int(u0), int(u1), int(u2),
-                                        int(u3), int(grad), int(stream) or None))
+def fd_imaging_accumulate_steps(grid, scale, mu, u, grad, stream=0):
+    """The imaging of adjoint steps n, n-1, ..., n-k+1 in one pass: mu = k
+    adjoint-state pointers (times n, n-1, ...), u = k + 2 forward-state
+    pointers (times n, n-1, ...), device memory."""
+    k = len(mu)
+    if len(u) != k + 2:
+        raise ValueError("need k + 2 forward states for k adjoint states")
+    mu_arr = (ctypes.c_void_p * max(k, 1))(*[int(p) for p in mu])
+    u_arr = (ctypes.c_void_p * len(u))(*[int(p) for p in u])
+    _check(lib().fd_imaging_accumulate_steps(grid, float(scale), k, mu_arr, u_arr, int(grad), int(stream) or None))
 
 
 def fd_operator_apply_imaging(op, n, dt, scale, u0, u1, u2, grad):

@@ -13,9 +13,10 @@ a segment buffer, and the imaging condition
     dJ/dm += -(1/dt^2) mu^n (u^n - 2u^{n-1} + u^{n-2})
 is accumulated in the same pass as every adjoint step where the tiled sweep
 injects the residual itself (fd_operator_apply_imaging: fused into the
-sweep); otherwise two adjoint steps run first and one pass images both
-(fd_imaging_accumulate2), which reads each forward state and the gradient
-once for the two steps.  Either way the gradient is the same bit for bit.
+sweep).  Otherwise up to four adjoint steps run first, out of place into a
+ring of six adjoint states, and one pass images them all
+(fd_imaging_accumulate_steps), reading each forward state and the gradient
+once for the four steps.  Either way the gradient is the same bit for bit.
 
 Every step of the path runs in libfdgb's kernels; torch provides the device
 memory (fields, checkpoints, the segment buffer) and the autograd plumbing.
@@ -83,6 +84,8 @@ class Propagator:
             self.hist = torch.zeros((self.nt + 2,) + ps, dtype=torch.float32, device="cuda")
         self.grad = fd.DenseData("grad", self.grid)
         self.stream = torch.cuda.current_stream().cuda_stream
+        # adjoint states of times t in ring[t % 6] (steps out of place, imaged four at a time)
+        self.mu_ring = torch.zeros((6,) + ps, dtype=torch.float32, device="cuda")
 
     def set_damping(self, eta):
         """Damping eta (held fixed by the gradient)."""
@@ -135,6 +138,7 @@ class Propagator:
         self.res.data[:, : self.res.npoint].copy_(residual)
         for s in self.mu.slots:
             s.zero_()
+        self.mu_ring.zero_()
         self.grad.slots[0].zero_()
         scale = -1.0 / (self.dt * self.dt)
         if self.k == 0:
@@ -165,24 +169,28 @@ class Propagator:
         state(t) is the device pointer of the forward state of time t, for
         t >= n_bot - 2."""
         gp = self.grad.slots[0].data_ptr()
-        paired = not fd.fd_operator_sources_fused(self.adj.handle)
+        if fd.fd_operator_sources_fused(self.adj.handle):
+            # the sweep images the state it writes, one step at a time
+            for n in range(n_top, n_bot - 1, -1):
+                if n >= 1:
+                    fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, state(n), state(n - 1),
+                                                 state(n - 2), gp)
+                else:
+                    self.adj.apply(n, 1, self.dt)
+            return
+        # up to four steps out of place into the ring, then one pass images
+        # them; the adjoint state of time 0 images nothing and is not computed
+        ring = self.mu_ring
+        lo = max(n_bot, 1)
         n = n_top
-        while n >= n_bot:
-            if paired and n - 1 >= max(n_bot, 1):
-                # steps n and n-1, then one pass images both; the adjoint
-                # state of time t is in slot t % 2
-                self.adj.apply(n - 1, 2, self.dt)
-                fd.fd_imaging_accumulate2(self.grid.handle, scale, self.mu.slots[n % 2].data_ptr(),
-                                          self.mu.slots[(n - 1) % 2].data_ptr(), state(n), state(n - 1),
-                                          state(n - 2), state(n - 3), gp, self.stream)
-                n -= 2
-            elif n >= 1:
-                fd.fd_operator_apply_imaging(self.adj.handle, n, self.dt, scale, state(n), state(n - 1),
-                                             state(n - 2), gp)
-                n -= 1
-            else:
-                self.adj.apply(n, 1, self.dt)
-                n -= 1
+        while n >= lo:
+            k = min(4, n - lo + 1)
+            for t in range(n, n - k, -1):
+                fd.fd_operator_step(self.adj.handle, t, self.dt, ring[(t + 1) % 6].data_ptr(),
+                                    ring[(t + 2) % 6].data_ptr(), ring[t % 6].data_ptr())
+            fd.fd_imaging_accumulate_steps(self.grid.handle, scale, [ring[(n - j) % 6].data_ptr() for j in range(k)],
+                                           [state(n - i) for i in range(k + 2)], gp, self.stream)
+            n -= k
 
 
 def _autograd_function():

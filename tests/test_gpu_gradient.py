@@ -155,41 +155,42 @@ def test_fused_imaging_equals_step_then_imaging(flags):
     assert np.abs(out[0][1] - grad0[..., :shape[2]].cpu().numpy()).max() > 0
 
 
-def test_paired_imaging_equals_two_single_passes():
-    """fd_imaging_accumulate2 (adjoint steps n and n-1 imaged in one pass)
-    equals fd_imaging_accumulate for step n, then for step n-1, bit for bit;
-    rows of 37 points take the scalar tail as well."""
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_imaging_steps_equal_single_passes(k):
+    """fd_imaging_accumulate_steps (adjoint steps n .. n-k+1 imaged in one
+    pass) equals fd_imaging_accumulate for step n, n-1, ... in turn, bit for
+    bit; rows of 37 points take the scalar tail as well."""
     import torch
     shape = (9, 7, 37)
     grid = fd.Grid(shape, (10.0,) * 3)
-    f = [torch.zeros(grid.padded_shape, dtype=torch.float32, device="cuda") for _ in range(7)]
+    f = [torch.zeros(grid.padded_shape, dtype=torch.float32, device="cuda") for _ in range(2 * k + 3)]
     for i, t in enumerate(f):
         t[..., :shape[2]].copy_(torch.from_numpy(wl.random_field(shape, 40 + i, smooth=1)))
-    mu_a, mu_b, u0, u1, u2, u3, g0 = f
+    mu, u, g0 = f[:k], f[k:2 * k + 2], f[-1]
     st = torch.cuda.current_stream().cuda_stream
     scale = -1.0 / 1e-3 ** 2
     g1, g2 = g0.clone(), g0.clone()
-    fd.fd_imaging_accumulate(grid.handle, scale, mu_a.data_ptr(), u0.data_ptr(), u1.data_ptr(), u2.data_ptr(),
-                             g1.data_ptr(), st)
-    fd.fd_imaging_accumulate(grid.handle, scale, mu_b.data_ptr(), u1.data_ptr(), u2.data_ptr(), u3.data_ptr(),
-                             g1.data_ptr(), st)
-    fd.fd_imaging_accumulate2(grid.handle, scale, mu_a.data_ptr(), mu_b.data_ptr(), u0.data_ptr(), u1.data_ptr(),
-                              u2.data_ptr(), u3.data_ptr(), g2.data_ptr(), st)
+    for j in range(k):
+        fd.fd_imaging_accumulate(grid.handle, scale, mu[j].data_ptr(), u[j].data_ptr(), u[j + 1].data_ptr(),
+                                 u[j + 2].data_ptr(), g1.data_ptr(), st)
+    fd.fd_imaging_accumulate_steps(grid.handle, scale, [t.data_ptr() for t in mu], [t.data_ptr() for t in u],
+                                   g2.data_ptr(), st)
     torch.cuda.synchronize()
     n2 = shape[2]
     assert torch.equal(g1[..., :n2], g2[..., :n2])
     assert not torch.equal(g2[..., :n2], g0[..., :n2])
     with pytest.raises(fd.FDError):
-        fd.fd_imaging_accumulate2(grid.handle, scale, mu_a.data_ptr(), mu_b.data_ptr(), u0.data_ptr(),
-                                  u1.data_ptr(), u2.data_ptr(), u3.data_ptr(), u3.data_ptr(), st)
+        fd.fd_imaging_accumulate_steps(grid.handle, scale, [t.data_ptr() for t in mu], [t.data_ptr() for t in u],
+                                       u[0].data_ptr(), st)
 
 
 @pytest.mark.parametrize("flags", [0, fd.FD_FLAG_PLAIN_KERNELS])
-def test_paired_backward_equals_per_step_imaging(flags):
+def test_grouped_backward_equals_per_step_imaging(flags):
     """Where the sweep does not inject the residual itself, the backward sweep
-    runs two adjoint steps and images both in one pass.  Its gradient equals
-    the per-step loop (fd_operator_apply_imaging at every step) bit for bit;
-    an odd step count leaves one step to image alone."""
+    runs up to four adjoint steps out of place and images them in one pass.
+    Its gradient equals the per-step loop (fd_operator_apply_imaging at every
+    step, in the operator's own slots) bit for bit; 61 steps leave a last group
+    of fewer than four."""
     import torch
     case = _case(seed=7, nt=61)
     shape, h, origin, m0, eta, dt, src_c, rec_c, src, d_obs, nt = case
@@ -197,7 +198,7 @@ def test_paired_backward_equals_per_step_imaging(flags):
     prop.set_damping(eta)
     prop.set_model(torch.from_numpy(m0).cuda())
     residual = prop.forward().clone() - torch.from_numpy(d_obs).cuda()
-    g_paired = prop.backward(residual).clone()
+    g_grouped = prop.backward(residual).clone()
     for s in prop.mu.slots:
         s.zero_()
     prop.grad.slots[0].zero_()
@@ -213,8 +214,8 @@ def test_paired_backward_equals_per_step_imaging(flags):
     prop.adj.sync()
     if flags & fd.FD_FLAG_PLAIN_KERNELS:
         assert not fd.fd_operator_sources_fused(prop.adj.handle)
-    assert torch.equal(g_paired, prop.grad.data)
-    assert float(g_paired.abs().max()) > 0
+    assert torch.equal(g_grouped, prop.grad.data)
+    assert float(g_grouped.abs().max()) > 0
 
 
 def test_receiver_lattice_is_injected_inside_the_chunked_sweep():
