@@ -140,3 +140,32 @@ def test_sparse_domain_check_before_device(L):
     with pytest.raises(fd.FDError) as e:
         fd.fd_grid_create((8, 1, 10), (2.0, 2.0, 2.0), (0.0, 0.0, 0.0))
     assert e.value.status == fd.FD_ERR_INVALID_ARG
+
+
+def test_imaging_steps_argument_checks(L):
+    """fd_imaging_accumulate_steps rejects a group size outside 1..4, null and
+    misaligned buffers and a gradient that aliases an input before it
+    launches anything (the pointers here are never dereferenced)."""
+    g = fd.fd_grid_create((8, 9, 10), (1.0,) * 3)
+    mu = [4096 * (i + 1) for i in range(4)]
+    u = [65536 * (i + 1) for i in range(6)]
+    grad = 1 << 24
+    cases = [
+        (([], u[:2], grad), fd.FD_ERR_INVALID_ARG),                      # k = 0
+        (([4096] * 5, [8192] * 7, grad), fd.FD_ERR_INVALID_ARG),         # k = 5
+        ((mu[:2], u[:4], 0), fd.FD_ERR_INVALID_ARG),                     # null grad
+        (([mu[0], 0], u[:4], grad), fd.FD_ERR_INVALID_ARG),              # null adjoint state
+        ((mu[:2], u[:3] + [0], grad), fd.FD_ERR_INVALID_ARG),            # null forward state
+        ((mu[:2], [u[0] + 4] + u[1:4], grad), fd.FD_ERR_LAYOUT),         # misaligned input
+        ((mu[:2], u[:4], grad + 8), fd.FD_ERR_LAYOUT),                   # misaligned grad
+        ((mu[:2], u[:4], u[3]), fd.FD_ERR_INVALID_ARG),                  # grad aliases an input
+    ]
+    for (m_, u_, gr), status in cases:
+        k = len(m_)
+        mu_arr = (ctypes.c_void_p * max(k, 1))(*m_)
+        u_arr = (ctypes.c_void_p * len(u_))(*u_)
+        rc = L.fd_imaging_accumulate_steps(g, -1.0, k, mu_arr, u_arr, gr, None)
+        assert rc == status, (k, rc, status, fd.fd_last_error())
+    with pytest.raises(ValueError):
+        fd.fd_imaging_accumulate_steps(g, -1.0, mu[:2], u[:3], grad)
+    fd.fd_grid_destroy(g)
